@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused FP64 cardiac stepper on GB300.
+
+Workload (one bench step): the two-field FitzHugh-Nagumo model of Sect. 2 on
+a 1024 x 1024 grid (dx = 0.04), 9-point isotropic Laplacian (alpha_d = 1/6),
+no-flux mirror ghosts, classic RK4 with dt = 4e-4, 10000 time steps from the
+seeded broken-wave state; one persistent kernel launch per bench step.
+Metric: FP64 giga cell-updates per second (GCUPS) and the fraction of the
+FP64-pipe roofline.  Also reported: the same metric end to end through the
+public API with host buffers, the other workloads (small grid, four-field
+model), and the CPU oracle on a bounded sample of the workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 GCUPS & % of HBM/FP64 roofline; batched and adjoint/JVP vs plain stepper"
+NX = NY = 1024
+STEPS_PER_RUN = 10000
+DT = 4e-4
+# Algorithmic FP64 flops per cell-update, FMA = 2 (per RK stage: 9-point
+# Laplacian 2 x 11, local terms 8, D scaling 2 x 2, combine 2 x 4; x 4 stages).
+FLOPS_PER_CELL_UPDATE = 168
+# Algorithmic HBM bytes per cell-update of a fused step: each field read and
+# written once (2 fields x 8 B x 2).
+BYTES_PER_CELL_UPDATE = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run 20 steps of the workload twice and exit (for ncu captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measure_fp64_peak():
+    """FP64 DFMA throughput of this GPU (TFLOP/s) from the library's probe."""
+    import ctypes
+    from paper_1309_1720_gb300 import _lib
+    L = _lib.lib()
+    rate = ctypes.c_double()
+    best = 0.0
+    for _ in range(3):
+        _lib.check(L.cg_measure_fp64_rate(0, 0, ctypes.byref(rate), None))
+        best = max(best, rate.value)
+    return 2.0 * best / 1e12, best
+
+
+def cpu_baseline(seconds_target=12.0):
+    """The oracle as it stands (single thread) on a bounded sample of the
+    workload: the same 1024^2 RK4 9-point problem for a few steps."""
+    import oracle as O
+    from paper_1309_1720_gb300 import inputs as I
+    z = I.fhn_broken_wave(NX, NY, seed=0)
+    p = O.problem(O.FHN, nx=NX, ny=NY, dx=0.04, stencil=O.ST9, alpha_d=1 / 6, scheme=O.RK4, dt=DT)
+    t = time.perf_counter()
+    z1 = O.step(p, z, 2)
+    per = (time.perf_counter() - t) / 2
+    n = int(max(3, min(200, seconds_target / max(per, 1e-6))))
+    t = time.perf_counter()
+    O.step(p, z1, n)
+    dt = time.perf_counter() - t
+    return {"value": NX * NY * n / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 steps of the 1024x1024 9-point two-field workload, single-threaded C oracle "
+                      "(-O2 -ffp-contract=off), rate extrapolated to the full run" % n,
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1309_1720_gb300 import inputs as I
+    z = I.fhn_broken_wave(NX, NY, seed=0)
+    p = O.problem(O.FHN, nx=NX, ny=NY, dx=0.04, stencil=O.ST9, alpha_d=1 / 6, scheme=O.RK4, dt=DT)
+    sample_steps = 10
+    for _ in range(args.warmup):
+        O.step(p, z, 1)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.step(p, z, sample_steps)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    val = NX * NY * sample_steps * args.steps / tot / 1e9
+    line = {
+        "metric": METRIC, "value": val, "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(),
+        "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                         "sample": "each step: %d RK4 time steps of the 1024x1024 9-point two-field workload "
+                                   "on the single-threaded C oracle" % sample_steps},
+        "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": "fhn-1024x1024-9pt-rk4-10000steps",
+            "model": "FitzHugh-Nagumo (eps, a1, a0) = (0.05, 1.5, -0.1), D = (1, 1.5)",
+            "grid": [NX, NY], "dx": 0.04, "stencil": "9-point isotropic, alpha_d = 1/6",
+            "bc": "no-flux mirror", "scheme": "RK4", "dt": DT, "time_steps_per_bench_step": STEPS_PER_RUN,
+            "ic": "seeded broken wave (seed 0)",
+            "l2": "flushed (256 MB write) between timed bench steps; the 80 MB working set is L2-resident "
+                  "within a run by design"}
+
+
+def secondary_rows(torch, plan_cls, I, api, peak_tflops):
+    """Short rate measurements of the other workloads (rate-based; truncated
+    step counts are stated)."""
+    rows = {}
+
+    def timed(plan, z, n, reps=3):
+        out = torch.empty_like(z)
+        plan.run(z, n, out=out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.run(z, n, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        plan.status()
+        return min(ts)
+
+    # 128^2 explicit Euler, 5-point, 1000 steps (launch/latency-bound size)
+    p = api.Problem(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
+    plan = plan_cls(p)
+    z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
+    t = timed(plan, z, 1000)
+    rows["fhn-128x128-5pt-euler-1000steps"] = {"gcups": 128 * 128 * 1000 / t / 1e9, "seconds": t}
+    plan.close()
+
+    # 2048^2 four-field model, anisotropic 9-point, RK4 (500 of the 5000 steps)
+    n, steps = 2048, 500
+    p = api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
+                    stencil=api.STENCIL9, scheme=api.RK4, dt=0.05)
+    plan = plan_cls(p)
+    z = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
+    t = timed(plan, z, steps, reps=2)
+    rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t,
+                                           "steps_timed": steps, "note": "rate of 500 of the 5000 steps"}
+    plan.close()
+    return rows
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1309_1720_gb300 import Plan, api, inputs as I
+
+    prob = api.Problem(model=api.FHN, nx=NX, ny=NY, dx=0.04, stencil=api.STENCIL9, alpha_d=1 / 6,
+                       scheme=api.RK4, dt=DT)
+    plan = Plan(prob)
+    z0_host = I.fhn_broken_wave(NX, NY, seed=0)
+    z0 = torch.from_numpy(z0_host).cuda()
+    out = torch.empty_like(z0)
+    ws_t = plan.workspace()
+
+    if args.profile_case:
+        for _ in range(2):
+            plan.run(z0, 20, out=out)
+        plan.status()
+        torch.cuda.synchronize()
+        print("profile case done")
+        return
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cells = NX * NY * STEPS_PER_RUN
+
+    peak_tflops, dfma_rate = measure_fp64_peak()
+
+    for _ in range(args.warmup):
+        plan.run(z0, STEPS_PER_RUN, out=out, stream=stream)
+    plan.status()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run(z0, STEPS_PER_RUN, out=out, stream=stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    plan.status()
+    secs = [a.elapsed_time(b) / 1e3 for a, b in times]
+    tot = sum(secs)
+    if ws > 1:
+        tt = torch.tensor([tot], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tot = float(tt.item())
+    value = ws * cells * args.steps / tot / 1e9
+    launch_s = statistics.median(secs)
+    achieved_tflops = FLOPS_PER_CELL_UPDATE * cells / launch_s / 1e12
+
+    # end to end through the public API: pinned host in, host out, every step
+    h_in = torch.from_numpy(z0_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(z0)
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_in.copy_(h_in, non_blocking=True)
+        plan.run(d_in, STEPS_PER_RUN, out=out, stream=stream)
+        h_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e2e_t.append((e0, e1))
+    barrier()
+    e2e_tot = sum(a.elapsed_time(b) / 1e3 for a, b in e2e_t)
+    if ws > 1:
+        tt = torch.tensor([e2e_tot], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(tt.item())
+    nbytes = z0.numel() * 8
+
+    rows = None
+    if not args.no_rows and rank == 0:
+        rows = secondary_rows(torch, Plan, I, api, peak_tflops)
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws >= 1 and args.gpus == 1:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "peak_source": "measured FP64 DFMA throughput of this GPU (library probe, 8 chains x "
+                                        "256 threads x 4 blocks/SM), FMA = 2 flops",
+                         "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                         "hbm_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
+                         "kernel": "k_stage<FHN, 9-point, RK4, 2 cells/lane> (persistent)"},
+            "e2e": {"value": ws * cells * args.steps / e2e_tot / 1e9, "unit": "GCUPS",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "wall_s_timed": t_wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        if rows is not None:
+            line["rows"] = rows
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

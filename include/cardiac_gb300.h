@@ -1,0 +1,184 @@
+/*
+ * cardiac_gb300.h -- C ABI of the GB300 FP64 cardiac reaction-diffusion stepper.
+ *
+ * The library advances the two-dimensional reaction-diffusion system
+ *
+ *     dz/dt = div(D grad z) + N[z],    z = (u, gates)            Eq. (rdeqn), Sect. 2
+ *
+ * on an nx x ny grid with no-flux boundaries (Eq. BC:N) imposed by ghost
+ * points that flip stencil displacements back into the grid (Sect. 3,
+ * Fig. 1), a 5-point or 9-point Laplacian (Eq. diffusion) and an explicit
+ * fixed-step integrator (explicit Euler, Heun or classic RK4, Sect. 3), in
+ * FP64 throughout, on one NVIDIA GB300 (sm_103a).  The problem statement
+ * follows the paper's: model and its parameters, grid with dx and dy,
+ * diffusivity D, time step dt, scheme, state in, state out, number of steps.
+ *
+ * Conventions for every entry point:
+ *  - Every state is a caller-owned DEVICE buffer of float64 laid out
+ *    [n_v][ny][nx] (field planes, row-major, x contiguous; no padding).
+ *  - The caller owns the stream (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) and the workspace (device memory of at least the
+ *    size the matching *_workspace_size call returns, 256-byte aligned).
+ *    The run path never allocates device memory.
+ *  - Calls are asynchronous on the stream unless stated otherwise.  They can
+ *    be captured into a CUDA graph (they issue only kernel launches,
+ *    cudaMemsetAsync and device-to-device cudaMemcpyAsync).
+ *  - Errors are returned as cg_status codes, never by abort or exception; a
+ *    human-readable message for the calling thread is available from
+ *    cg_last_error().  Errors detected on the device (non-finite output, a
+ *    grid barrier that gave up waiting) are recorded in a status word inside
+ *    the workspace and read back with cg_read_status().
+ *  - A plan is immutable after creation and may be shared between threads
+ *    and streams, provided each concurrent run has its own workspace.
+ */
+#ifndef CARDIAC_GB300_H
+#define CARDIAC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG_ABI_VERSION 1
+
+typedef enum cg_status {
+    CG_OK = 0,
+    CG_EINVAL = 1,          /* invalid argument (message in cg_last_error) */
+    CG_ENOMEM = 2,          /* host or plan-time device allocation failed */
+    CG_ECUDA = 3,           /* a CUDA runtime call failed */
+    CG_EUNSTABLE = 4,       /* dt above the scheme's linear diffusive stability bound */
+    CG_ENAN = 5,            /* a non-finite value was written (device status) */
+    CG_ETIMEOUT = 6,        /* a bounded device wait gave up (device status) */
+    CG_EUNSUPPORTED = 7     /* valid request this build does not implement */
+} cg_status;
+
+/* Models (Sect. 2).  CG_DIFFUSION is the linear case N = 0 with one field,
+ * useful for checking the stencil and integrators against closed forms.
+ * CG_KARMA is reserved: its constants are not printed in the paper. */
+enum { CG_FHN = 0, CG_BOCF = 1, CG_KARMA = 2, CG_DIFFUSION = 3 };
+/* Laplacian (Eq. diffusion): 5-point, or 9-point with diagonal weight alpha_d. */
+enum { CG_STENCIL5 = 0, CG_STENCIL9 = 1 };
+/* Ghost points (Fig. 1): MIRROR maps index -1 to 1 and n to n-2 (the
+ * displacement is flipped back into the grid); CLAMP maps -1 to 0, n to n-1. */
+enum { CG_BC_MIRROR = 0, CG_BC_CLAMP = 1 };
+/* Explicit integrators of Sect. 3. */
+enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2 };
+
+/* cg_problem.flags */
+#define CG_FLAG_ALLOW_UNSTABLE   (1u << 0)  /* skip the dt stability check */
+#define CG_FLAG_PER_STAGE_LAUNCH (1u << 1)  /* one kernel launch per RK stage instead of one
+                                               persistent cooperative launch per run */
+#define CG_FLAG_TEST_STUCK_BARRIER (1u << 8) /* testing only: the first grid barrier waits for
+                                               one block more than exist, so it must give up
+                                               after barrier_timeout_s and report CG_ETIMEOUT */
+
+/* Device status bits (cg_read_status). */
+#define CG_DEV_NONFINITE 1u   /* a non-finite value was stored */
+#define CG_DEV_TIMEOUT   2u   /* a grid barrier wait gave up */
+
+typedef struct cg_problem {
+    int32_t abi_version;   /* must be CG_ABI_VERSION */
+    int32_t model;         /* CG_FHN, CG_BOCF or CG_DIFFUSION */
+    int64_t nx, ny;        /* grid size, each >= 2 (N x N in the paper) */
+    double dx, dy;         /* grid spacing (dx = dy = 0.04 for FHN, 0.03 cm for BOCF) */
+    double Dxx[4], Dyy[4]; /* per-field diagonal diffusion tensor; 0 = field not diffusive.
+                              FHN: (1, delta = 1.5); BOCF: (1.171e-3 cm^2/ms, 0, 0, 0) */
+    int32_t stencil;       /* CG_STENCIL5 / CG_STENCIL9 */
+    int32_t bc;            /* CG_BC_MIRROR / CG_BC_CLAMP */
+    int32_t scheme;        /* CG_EULER / CG_HEUN / CG_RK4 */
+    uint32_t flags;        /* CG_FLAG_* */
+    double alpha_d;        /* 9-point diagonal weight (axial weight 1 - 2 alpha_d); ignored for 5-point */
+    double dt;             /* fixed time step */
+    const double *params;  /* host array of cg_n_params(model) model constants, copied at plan
+                              creation; NULL selects the defaults (cg_default_params) */
+    int32_t n_params;      /* length of params (ignored when params is NULL) */
+    int32_t reserved0;
+    double barrier_timeout_s; /* bound on any device-side wait; <= 0 selects 10 s */
+} cg_problem;
+
+/* Optional launch shape (the autotuner's search space).  Zero fields take
+ * the library's defaults. */
+typedef struct cg_tuning {
+    int32_t cells_x;       /* cells per lane along x: 1 or 2 (warp tile width 32 or 64) */
+    int32_t rows;          /* rows per warp tile, >= 1 */
+    int32_t threads;       /* threads per block: 128, 256 or 512 */
+    int32_t blocks_per_sm; /* persistent blocks per SM, >= 1 (capped by occupancy) */
+} cg_tuning;
+
+typedef struct cg_plan_s *cg_plan;
+
+/* ---------------------------------------------------------------- plans */
+
+/* Validate a problem and build an immutable plan (coefficients, tile table,
+ * launch shape).  Returns CG_EINVAL for a bad argument and CG_EUNSTABLE when
+ * dt exceeds the linear bound 2/rho (Euler, Heun) or 2.785/rho (RK4), rho
+ * the spectral radius of the diffusion operator, unless
+ * CG_FLAG_ALLOW_UNSTABLE is set.  Allocates a small device table on the
+ * current device; *out is NULL on error. */
+cg_status cg_plan_create(const cg_problem *prob, cg_plan *out);
+
+/* Same with an explicit launch shape (tuning may be NULL). */
+cg_status cg_plan_create_tuned(const cg_problem *prob, const cg_tuning *tuning, cg_plan *out);
+
+/* Build one plan for n_inst independent problems (uneven nx, ny and D
+ * allowed; the same model, stencil, bc, scheme, dt, params and flags).  The
+ * instances' states are packed back to back in one buffer: instance i starts
+ * at element offset offsets[i] (cg_batch_offsets), each in the [n_v][ny][nx]
+ * layout.  All instances advance together in one persistent launch. */
+cg_status cg_batch_create(const cg_problem *probs, int32_t n_inst, const cg_tuning *tuning,
+                          cg_plan *out);
+
+/* Element offsets of the packed batch layout: offsets[0..n_inst], the last
+ * entry being the total number of doubles.  A single-instance plan reports
+ * {0, n_v*nx*ny}. */
+cg_status cg_batch_offsets(cg_plan plan, int64_t *offsets);
+
+/* Number of instances of a plan (1 for cg_plan_create). */
+int32_t cg_plan_n_instances(cg_plan plan);
+
+/* Release a plan and its device table.  NULL is accepted. */
+cg_status cg_plan_destroy(cg_plan plan);
+
+/* Bytes of device workspace that cg_run needs for this plan. */
+cg_status cg_workspace_size(cg_plan plan, size_t *bytes);
+
+/* ------------------------------------------------------------- stepping */
+
+/* Advance the state(s) by n_steps >= 0 explicit steps (Sect. 3) of
+ * dz/dt = D L z + N[z].  z_in and z_out are device buffers in the plan's
+ * layout (packed for a batch); z_in == z_out is allowed, partial overlap is
+ * not.  n_steps == 0 copies z_in to z_out.  Clears the device status word. */
+cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
+                 void *workspace, void *stream);
+
+/* Synchronise the stream and return the device status bits (CG_DEV_*)
+ * recorded by the last run that used this workspace.  Returns CG_ENAN or
+ * CG_ETIMEOUT when the matching bit is set, CG_OK otherwise. */
+cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags);
+
+/* ----------------------------------------------------------------- misc */
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *cg_last_error(void);
+
+/* Number of fields n_v of a model (2 FHN, 4 BOCF, 1 diffusion), -1 if unknown. */
+int32_t cg_n_fields(int32_t model);
+
+/* Number of model constants (3 FHN: eps, a1, a0; 29 BOCF; 0 diffusion). */
+int32_t cg_n_params(int32_t model);
+
+/* Write the default constants of a model to out[0 .. cg_n_params(model)-1]
+ * (host memory).  FHN: Sect. 2 values; BOCF: the epicardial set of the
+ * model the paper cites, then k = 28.4 for H_k. */
+cg_status cg_default_params(int32_t model, double *out);
+
+/* CG_ABI_VERSION of the loaded library. */
+int32_t cg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CARDIAC_GB300_H */

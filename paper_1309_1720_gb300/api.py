@@ -1,0 +1,189 @@
+"""Python binding of the GB300 FP64 cardiac stepper.
+
+Thin wrappers over the C ABI (include/cardiac_gb300.h): problems become
+``cg_problem`` records, torch CUDA tensors supply device pointers and
+streams, and every step of the computation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import CProblem, CTuning, check
+
+# enums of cardiac_gb300.h
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENAN, ETIMEOUT, EUNSUPPORTED = range(8)
+FHN, BOCF, KARMA, DIFFUSION = 0, 1, 2, 3
+STENCIL5, STENCIL9 = 0, 1
+MIRROR, CLAMP = 0, 1
+EULER, HEUN, RK4 = 0, 1, 2
+FLAG_ALLOW_UNSTABLE = 1 << 0
+FLAG_PER_STAGE_LAUNCH = 1 << 1
+FLAG_TEST_STUCK_BARRIER = 1 << 8
+DEV_NONFINITE, DEV_TIMEOUT = 1, 2
+ABI_VERSION = 1
+
+_DEFAULT_D = {FHN: (1.0, 1.5), BOCF: (1.171e-3,), DIFFUSION: (1.0,)}
+
+
+def n_fields(model: int) -> int:
+    return int(_lib.lib().cg_n_fields(model))
+
+
+def n_params(model: int) -> int:
+    return int(_lib.lib().cg_n_params(model))
+
+
+def default_params(model: int):
+    n = n_params(model)
+    buf = (ctypes.c_double * max(n, 1))()
+    check(_lib.lib().cg_default_params(model, buf))
+    return [buf[i] for i in range(n)]
+
+
+@dataclass
+class Problem:
+    """One grid instance: the paper's problem statement (model, grid, D, dt,
+    scheme).  ``D`` sets Dxx = Dyy per field; ``Dyy`` overrides for an
+    anisotropic diagonal tensor."""
+    model: int = FHN
+    nx: int = 128
+    ny: int = 128
+    dx: float = 0.04
+    dy: Optional[float] = None
+    D: Optional[Sequence[float]] = None
+    Dyy: Optional[Sequence[float]] = None
+    stencil: int = STENCIL5
+    bc: int = MIRROR
+    scheme: int = EULER
+    alpha_d: float = 1.0 / 6.0
+    dt: float = 2e-4
+    params: Optional[Sequence[float]] = None
+    flags: int = 0
+    barrier_timeout_s: float = 0.0
+    _keep: list = field(default_factory=list, repr=False, compare=False)
+
+    def to_c(self) -> CProblem:
+        c = CProblem()
+        c.abi_version = ABI_VERSION
+        c.model = self.model
+        c.nx, c.ny = int(self.nx), int(self.ny)
+        c.dx = float(self.dx)
+        c.dy = float(self.dx if self.dy is None else self.dy)
+        Dxx = list(_DEFAULT_D.get(self.model, ()) if self.D is None else self.D)
+        Dyy = list(Dxx if self.Dyy is None else self.Dyy)
+        for i in range(4):
+            c.Dxx[i] = float(Dxx[i]) if i < len(Dxx) else 0.0
+            c.Dyy[i] = float(Dyy[i]) if i < len(Dyy) else 0.0
+        c.stencil, c.bc, c.scheme = self.stencil, self.bc, self.scheme
+        c.flags = self.flags
+        c.alpha_d = float(self.alpha_d)
+        c.dt = float(self.dt)
+        if self.params is not None:
+            arr = (ctypes.c_double * len(self.params))(*[float(x) for x in self.params])
+            self._keep = [arr]
+            c.params = ctypes.cast(arr, _lib.c_dp)
+            c.n_params = len(self.params)
+        else:
+            c.params = None
+            c.n_params = 0
+        c.barrier_timeout_s = float(self.barrier_timeout_s)
+        return c
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """An immutable stepping plan for one instance or a packed batch."""
+
+    def __init__(self, problems, tuning: Optional[dict] = None):
+        L = _lib.lib()
+        single = isinstance(problems, Problem)
+        self.problems = [problems] if single else list(problems)
+        self.model = self.problems[0].model
+        self.nv = n_fields(self.model)
+        cprobs = (CProblem * len(self.problems))(*[p.to_c() for p in self.problems])
+        tun = None
+        if tuning:
+            tun = CTuning(int(tuning.get("cells_x", 0)), int(tuning.get("rows", 0)),
+                          int(tuning.get("threads", 0)), int(tuning.get("blocks_per_sm", 0)))
+        h = ctypes.c_void_p()
+        if single:
+            st = L.cg_plan_create_tuned(cprobs, ctypes.byref(tun) if tun else None, ctypes.byref(h))
+        else:
+            st = L.cg_batch_create(cprobs, len(self.problems), ctypes.byref(tun) if tun else None,
+                                   ctypes.byref(h))
+        check(st)
+        self._h = h
+        n = L.cg_plan_n_instances(h)
+        offs = (ctypes.c_int64 * (n + 1))()
+        check(L.cg_batch_offsets(h, offs))
+        self.offsets = [int(offs[i]) for i in range(n + 1)]
+        sz = ctypes.c_size_t()
+        check(L.cg_workspace_size(h, ctypes.byref(sz)))
+        self.workspace_bytes = int(sz.value)
+        self._ws = None
+
+    # -- resources
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace(self) -> torch.Tensor:
+        if self._ws is None:
+            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.lib().cg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout helpers
+    def shape(self, i: int = 0):
+        p = self.problems[i]
+        return (self.nv, int(p.ny), int(p.nx))
+
+    def pack(self, states) -> torch.Tensor:
+        """Concatenate per-instance [n_v, ny, nx] tensors into the packed layout."""
+        return torch.cat([torch.as_tensor(s, dtype=torch.float64).reshape(-1) for s in states]).cuda()
+
+    def unpack(self, packed: torch.Tensor):
+        return [packed[self.offsets[i]:self.offsets[i + 1]].view(self.shape(i))
+                for i in range(len(self.problems))]
+
+    # -- stepping
+    def run(self, z_in: torch.Tensor, n_steps: int, out: Optional[torch.Tensor] = None,
+            stream=None, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Advance by n_steps; returns ``out`` (allocated if None)."""
+        assert z_in.is_cuda and z_in.dtype == torch.float64 and z_in.is_contiguous()
+        assert z_in.numel() == self.offsets[-1], "state has %d elements, plan expects %d" % (
+            z_in.numel(), self.offsets[-1])
+        if out is None:
+            out = torch.empty_like(z_in)
+        ws = self.workspace() if workspace is None else workspace
+        check(_lib.lib().cg_run(self._h, z_in.data_ptr(), out.data_ptr(), int(n_steps), ws.data_ptr(),
+                                _stream_handle(stream)))
+        return out
+
+    def status(self, stream=None, workspace: Optional[torch.Tensor] = None, raise_on_error: bool = True) -> int:
+        ws = self.workspace() if workspace is None else workspace
+        flags = ctypes.c_uint32()
+        st = _lib.lib().cg_read_status(self._h, ws.data_ptr(), _stream_handle(stream), ctypes.byref(flags))
+        if raise_on_error:
+            check(st)
+        return int(flags.value)

@@ -1,0 +1,576 @@
+// Host side of libcardiac_gb300.so: plan validation, stencil and model
+// coefficient folding, tile tables, workspace layout, kernel launches and
+// the device status word.  Declarations: include/cardiac_gb300.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cg_internal.h"
+
+#define CG_API extern "C" __attribute__((visibility("default")))
+
+using cgk::Inst;
+using cgk::RunArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+cg_status fail(cg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+cg_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(CG_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int n_fields(int model)
+{
+    switch (model) {
+    case CG_FHN: return 2;
+    case CG_BOCF: return 4;
+    case CG_DIFFUSION: return 1;
+    default: return -1;
+    }
+}
+
+int n_diffusive(int model)
+{
+    switch (model) {
+    case CG_FHN: return 2;
+    case CG_BOCF: return 1;
+    case CG_DIFFUSION: return 1;
+    default: return 0;
+    }
+}
+
+int n_params(int model)
+{
+    switch (model) {
+    case CG_FHN: return 3;
+    case CG_BOCF: return 29;
+    case CG_DIFFUSION: return 0;
+    default: return -1;
+    }
+}
+
+int n_stages(int scheme)
+{
+    return scheme == CG_EULER ? 1 : scheme == CG_HEUN ? 2 : 4;
+}
+
+// Default constants.  FHN: (eps, a1, a0) of Sect. 2.  BOCF: epicardial set
+// of the minimal model cited in Sect. 2 (order: uo uu thv thw thvm tho tv1m
+// tv2m tvp tw1m tw2m kwm uwm twp tfi to1 to2 tso1 tso2 kso uso ts1 ts2 ks us
+// tsi twinf winfstar), then the H_k sharpness k = 28.4 of Sect. 2.
+void default_params(int model, double *out)
+{
+    if (model == CG_FHN) {
+        const double p[3] = {0.05, 1.5, -0.1};
+        std::memcpy(out, p, sizeof p);
+    } else if (model == CG_BOCF) {
+        const double p[29] = {0.0,    1.55,   0.3,     0.13,   0.006,  0.006, 60.0, 1150.0,
+                              1.4506, 60.0,   15.0,    65.0,   0.03,   200.0, 0.11, 400.0,
+                              6.0,    30.0181, 0.9957, 2.0458, 0.65,   2.7342, 16.0, 2.0994,
+                              0.9087, 1.8875, 0.07,    0.94,   28.4};
+        std::memcpy(out, p, sizeof p);
+    }
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct cg_plan_s {
+    int32_t model = 0, stencil = 0, bc = 0, scheme = 0, nv = 0, ns = 0;
+    uint32_t flags = 0;
+    double dt = 0;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<Inst> inst;          // in tile order
+    std::vector<int64_t> offsets;    // packed offsets in user order (n_inst + 1)
+    std::vector<int32_t> order;      // user index -> tile-order index
+    Inst *d_inst = nullptr;
+    int32_t n_tiles = 0;
+    int32_t cx = 2, rows = 4, threads = 256, bpsm = 1;
+    int64_t scratch_elems = 0;
+    double mp[cgk::NMP] = {};
+    double cacc[4] = {}, cy[4] = {};
+    uint64_t timeout_ns = 0;
+    const void *kernel = nullptr;
+    int nblocks = 0;
+};
+
+namespace {
+
+const void *lookup_kernel(int model, int stencil, int scheme, int cx)
+{
+    switch (model) {
+    case CG_FHN: return cgk::fwd_kernel_fhn(stencil, scheme, cx);
+    case CG_BOCF: return cgk::fwd_kernel_bocf(stencil, scheme, cx);
+    case CG_DIFFUSION: return cgk::fwd_kernel_diff(stencil, scheme, cx);
+    default: return nullptr;
+    }
+}
+
+// Weights of D_f L for one field: Dxx d_xx + Dyy d_yy + kappa h^2 d_xx d_yy
+// with kappa = alpha_d (a + b) / 2 (Eq. diffusion; isotropic D recovers the
+// paper's alpha_a = 1 - 2 alpha_d, alpha_00 = -4 (alpha_a + alpha_d)).
+void stencil_weights(const cg_problem &p, int f, double &wx, double &wy, double &wd, double &wc)
+{
+    const double a = p.Dxx[f] / (p.dx * p.dx);
+    const double b = p.Dyy[f] / (p.dy * p.dy);
+    const double kappa = (p.stencil == CG_STENCIL9) ? p.alpha_d * (a + b) / 2.0 : 0.0;
+    wx = a - 2.0 * kappa;
+    wy = b - 2.0 * kappa;
+    wd = kappa;
+    wc = -2.0 * a - 2.0 * b + 4.0 * kappa;
+}
+
+// Largest |eigenvalue| of D_f L: the symbol a ex + b ey + kappa ex ey with
+// ex, ey in [-4, 0] is bilinear, so the extremes sit at the corners.
+double spectral_radius(const cg_problem &p, int f)
+{
+    const double a = p.Dxx[f] / (p.dx * p.dx);
+    const double b = p.Dyy[f] / (p.dy * p.dy);
+    const double kappa = (p.stencil == CG_STENCIL9) ? p.alpha_d * (a + b) / 2.0 : 0.0;
+    return std::max({4.0 * a, 4.0 * b, std::fabs(-4.0 * a - 4.0 * b + 16.0 * kappa)});
+}
+
+cg_status validate(const cg_problem *p, int idx)
+{
+    if (!p) return fail(CG_EINVAL, "problem %d is NULL", idx);
+    if (p->abi_version != CG_ABI_VERSION)
+        return fail(CG_EINVAL, "problem %d: abi_version %d, library speaks %d", idx, p->abi_version,
+                    CG_ABI_VERSION);
+    if (p->model == CG_KARMA)
+        return fail(CG_EUNSUPPORTED, "problem %d: the Karma model's constants are not in the paper; "
+                                     "model not built", idx);
+    const int nv = n_fields(p->model);
+    if (nv < 0) return fail(CG_EINVAL, "problem %d: unknown model %d", idx, p->model);
+    if (p->nx < 2 || p->ny < 2 || p->nx > (1 << 28) || p->ny > (1 << 28))
+        return fail(CG_EINVAL, "problem %d: grid %lld x %lld outside [2, 2^28]", idx, (long long)p->nx,
+                    (long long)p->ny);
+    if ((double)p->nx * (double)p->ny * nv > 4.0e12)
+        return fail(CG_EINVAL, "problem %d: grid too large", idx);
+    if (!(p->dx > 0) || !(p->dy > 0) || !finite(p->dx) || !finite(p->dy))
+        return fail(CG_EINVAL, "problem %d: dx, dy must be positive and finite", idx);
+    if (!(p->dt > 0) || !finite(p->dt)) return fail(CG_EINVAL, "problem %d: dt must be positive", idx);
+    if (p->stencil != CG_STENCIL5 && p->stencil != CG_STENCIL9)
+        return fail(CG_EINVAL, "problem %d: unknown stencil %d", idx, p->stencil);
+    if (p->stencil == CG_STENCIL9 && (!finite(p->alpha_d) || p->alpha_d < 0 || p->alpha_d > 0.25))
+        return fail(CG_EINVAL, "problem %d: alpha_d %g outside [0, 1/4]", idx, p->alpha_d);
+    if (p->bc != CG_BC_MIRROR && p->bc != CG_BC_CLAMP)
+        return fail(CG_EINVAL, "problem %d: unknown boundary mode %d", idx, p->bc);
+    if (p->scheme != CG_EULER && p->scheme != CG_HEUN && p->scheme != CG_RK4)
+        return fail(CG_EINVAL, "problem %d: unknown scheme %d", idx, p->scheme);
+    const int nd = n_diffusive(p->model);
+    for (int f = 0; f < 4; ++f) {
+        if (!finite(p->Dxx[f]) || !finite(p->Dyy[f]) || p->Dxx[f] < 0 || p->Dyy[f] < 0)
+            return fail(CG_EINVAL, "problem %d: D of field %d must be finite and >= 0", idx, f);
+        if (f >= nd && (p->Dxx[f] != 0 || p->Dyy[f] != 0))
+            return fail(CG_EUNSUPPORTED, "problem %d: field %d of this model does not diffuse", idx, f);
+    }
+    if (p->params && p->n_params != n_params(p->model))
+        return fail(CG_EINVAL, "problem %d: %d params given, model takes %d", idx, p->n_params,
+                    n_params(p->model));
+    if (p->params)
+        for (int i = 0; i < p->n_params; ++i)
+            if (!finite(p->params[i])) return fail(CG_EINVAL, "problem %d: param %d not finite", idx, i);
+    if (!(p->flags & CG_FLAG_ALLOW_UNSTABLE)) {
+        const double bound = (p->scheme == CG_RK4) ? 2.785 : 2.0;
+        double rho = 0;
+        for (int f = 0; f < nd; ++f) rho = std::max(rho, spectral_radius(*p, f));
+        if (rho * p->dt > bound * (1.0 + 1e-12))
+            return fail(CG_EUNSTABLE, "problem %d: dt %g exceeds the linear diffusive bound %g", idx, p->dt,
+                        bound / rho);
+    }
+    return CG_OK;
+}
+
+void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
+{
+    double prm[32] = {};
+    if (p.params) std::memcpy(prm, p.params, sizeof(double) * p.n_params);
+    else default_params(p.model, prm);
+    for (int f = 0; f < cgk::MAXF; ++f) {
+        if (f < n_diffusive(p.model)) stencil_weights(p, f, I.wx[f], I.wy[f], I.wd[f], I.wc[f]);
+        else I.wx[f] = I.wy[f] = I.wd[f] = I.wc[f] = 0.0;
+    }
+    std::memset(I.mi, 0, sizeof I.mi);
+    std::memset(P.mp, 0, sizeof P.mp);
+    if (p.model == CG_FHN) {
+        const double eps = prm[0], a1 = prm[1], a0 = prm[2];
+        P.mp[0] = eps;
+        P.mp[1] = -eps * a0;
+        I.mi[0] = 1.0 + I.wc[0];
+        I.mi[1] = I.wc[1] - eps * a1;
+    } else if (p.model == CG_DIFFUSION) {
+        I.mi[0] = I.wc[0];
+    } else {  // BOCF, layout of cg_stepper.cuh
+        for (int i = 0; i < 29; ++i) P.mp[i] = prm[i];
+        const double k = prm[28];
+        P.mp[29] = 0.5 - k * prm[2];    // thv
+        P.mp[30] = 0.5 - k * prm[3];    // thw
+        P.mp[31] = 0.5 - k * prm[4];    // thvm
+        P.mp[32] = 0.5 - k * prm[5];    // tho
+        P.mp[33] = prm[7] - prm[6];     // tv2m - tv1m
+        P.mp[34] = prm[16] - prm[15];   // to2 - to1
+        P.mp[35] = prm[22] - prm[21];   // ts2 - ts1
+        P.mp[36] = 1.0 / prm[14];       // 1/tfi
+        P.mp[37] = 1.0 / prm[25];       // 1/tsi
+        P.mp[38] = 1.0 / prm[8];        // 1/tvp
+        P.mp[39] = 1.0 / prm[13];       // 1/twp
+        P.mp[40] = 1.0 / prm[26];       // 1/twinf
+        I.mi[0] = I.wc[0];
+    }
+}
+
+bool same_config(const cg_problem &a, const cg_problem &b)
+{
+    if (a.model != b.model || a.stencil != b.stencil || a.bc != b.bc || a.scheme != b.scheme ||
+        a.dt != b.dt || a.flags != b.flags || a.barrier_timeout_s != b.barrier_timeout_s)
+        return false;
+    if (a.stencil == CG_STENCIL9 && a.alpha_d != b.alpha_d) return false;
+    if ((a.params == nullptr) != (b.params == nullptr)) return false;
+    if (a.params)
+        for (int i = 0; i < a.n_params; ++i)
+            if (a.params[i] != b.params[i]) return false;
+    return true;
+}
+
+cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tune, cg_plan *out)
+{
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!probs || n_inst < 1) return fail(CG_EINVAL, "need at least one problem");
+    for (int i = 0; i < n_inst; ++i) {
+        cg_status st = validate(&probs[i], i);
+        if (st != CG_OK) return st;
+        if (i > 0 && !same_config(probs[0], probs[i]))
+            return fail(CG_EINVAL, "problem %d: batch instances must share model, stencil, bc, scheme, "
+                                   "dt, params and flags", i);
+    }
+    const cg_problem &p0 = probs[0];
+    cg_plan_s *P = new (std::nothrow) cg_plan_s();
+    if (!P) return fail(CG_ENOMEM, "plan allocation failed");
+    P->model = p0.model;
+    P->stencil = p0.stencil;
+    P->bc = p0.bc;
+    P->scheme = p0.scheme;
+    P->nv = n_fields(p0.model);
+    P->ns = n_stages(p0.scheme);
+    P->flags = p0.flags;
+    P->dt = p0.dt;
+    const double tmo = p0.barrier_timeout_s > 0 ? p0.barrier_timeout_s : 10.0;
+    P->timeout_ns = (uint64_t)(std::min(tmo, 3600.0) * 1e9);
+
+    // launch shape
+    int64_t max_n = 0;
+    for (int i = 0; i < n_inst; ++i) max_n = std::max<int64_t>(max_n, probs[i].nx);
+    P->cx = (max_n >= 64) ? 2 : 1;
+    P->rows = 4;
+    P->threads = 256;
+    P->bpsm = 2;
+    if (tune) {
+        if (tune->cells_x) P->cx = tune->cells_x;
+        if (tune->rows) P->rows = tune->rows;
+        if (tune->threads) P->threads = tune->threads;
+        if (tune->blocks_per_sm) P->bpsm = tune->blocks_per_sm;
+    }
+    if ((P->cx != 1 && P->cx != 2) || P->rows < 1 || P->rows > 4096 ||
+        (P->threads != 128 && P->threads != 256 && P->threads != 512) || P->bpsm < 1 || P->bpsm > 8) {
+        delete P;
+        return fail(CG_EINVAL, "tuning out of range (cells_x 1|2, rows >= 1, threads 128|256|512, "
+                               "blocks_per_sm 1..8)");
+    }
+    P->kernel = lookup_kernel(P->model, P->stencil, P->scheme, P->cx);
+    if (!P->kernel) {
+        delete P;
+        return fail(CG_EUNSUPPORTED, "no kernel for this model/stencil/scheme");
+    }
+
+    // instances: packed offsets in user order, tiles largest-first
+    P->offsets.resize(n_inst + 1);
+    P->offsets[0] = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        int64_t sz = (int64_t)P->nv * probs[i].nx * probs[i].ny;
+        P->offsets[i + 1] = P->offsets[i] + sz;
+    }
+    std::vector<int32_t> ord(n_inst);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        return probs[a].nx * probs[a].ny > probs[b].nx * probs[b].ny;
+    });
+    P->order.assign(n_inst, 0);
+    P->inst.resize(n_inst);
+    const int tw = 32 * P->cx;
+    int64_t tiles = 0, scratch = 0;
+    for (int k = 0; k < n_inst; ++k) {
+        const int i = ord[k];
+        P->order[i] = k;
+        const cg_problem &p = probs[i];
+        Inst &I = P->inst[k];
+        std::memset(&I, 0, sizeof I);
+        I.nx = (int32_t)p.nx;
+        I.ny = (int32_t)p.ny;
+        I.tiles_x = (int32_t)((p.nx + tw - 1) / tw);
+        I.tiles_y = (int32_t)((p.ny + P->rows - 1) / P->rows);
+        I.tile_begin = (int32_t)tiles;
+        I.off = P->offsets[i];
+        I.vec_ok = ((p.nx % 2) == 0 && (I.off % 2) == 0) ? 1 : 0;
+        I.ws_off = scratch;
+        fold_constants(*P, p, I);
+        tiles += (int64_t)I.tiles_x * I.tiles_y;
+        int64_t blk = (int64_t)cgk::SCRATCH_PLANES * P->nv * p.nx * p.ny;
+        scratch += (blk + 31) / 32 * 32;     // keep blocks 256-byte aligned
+    }
+    if (tiles > 0x7fffffff) {
+        delete P;
+        return fail(CG_EINVAL, "too many tiles (%lld)", (long long)tiles);
+    }
+    P->n_tiles = (int32_t)tiles;
+    P->scratch_elems = scratch;
+
+    // Runge-Kutta combine weights (Sect. 3): acc += b_s dt F, Y_{s+1} = z + a dt F
+    const double dt = P->dt;
+    if (P->scheme == CG_EULER) {
+        P->cacc[0] = dt;
+    } else if (P->scheme == CG_HEUN) {
+        P->cacc[0] = dt / 2; P->cacc[1] = dt / 2;
+        P->cy[0] = dt;
+    } else {
+        P->cacc[0] = dt / 6; P->cacc[1] = dt / 3; P->cacc[2] = dt / 3; P->cacc[3] = dt / 6;
+        P->cy[0] = dt / 2; P->cy[1] = dt / 2; P->cy[2] = dt;
+    }
+
+    // device table and persistent grid
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, P->kernel, P->threads, 0);
+    if (e == cudaSuccess && occ < 1) {
+        delete P;
+        return fail(CG_EUNSUPPORTED, "kernel cannot run with %d threads per block", P->threads);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_inst, sizeof(Inst) * n_inst);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_inst, P->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (P->d_inst) cudaFree(P->d_inst);
+        delete P;
+        return cuda_fail(e, "plan creation");
+    }
+    P->nblocks = P->num_sms * std::min(P->bpsm, occ);
+    *out = P;
+    g_err.clear();
+    return CG_OK;
+}
+
+cg_status check_plan_device(cg_plan P)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != P->device) return fail(CG_EINVAL, "plan was made on device %d, current device is %d", P->device, dev);
+    return CG_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+CG_API cg_status cg_plan_create(const cg_problem *prob, cg_plan *out)
+{
+    return make_plan(prob, 1, nullptr, out);
+}
+
+CG_API cg_status cg_plan_create_tuned(const cg_problem *prob, const cg_tuning *tuning, cg_plan *out)
+{
+    return make_plan(prob, 1, tuning, out);
+}
+
+CG_API cg_status cg_batch_create(const cg_problem *probs, int32_t n_inst, const cg_tuning *tuning,
+                                 cg_plan *out)
+{
+    return make_plan(probs, n_inst, tuning, out);
+}
+
+CG_API cg_status cg_batch_offsets(cg_plan plan, int64_t *offsets)
+{
+    if (!plan || !offsets) return fail(CG_EINVAL, "NULL argument");
+    std::copy(plan->offsets.begin(), plan->offsets.end(), offsets);
+    return CG_OK;
+}
+
+CG_API int32_t cg_plan_n_instances(cg_plan plan)
+{
+    return plan ? (int32_t)plan->inst.size() : 0;
+}
+
+CG_API cg_status cg_plan_destroy(cg_plan plan)
+{
+    if (!plan) return CG_OK;
+    if (plan->d_inst) cudaFree(plan->d_inst);
+    delete plan;
+    return CG_OK;
+}
+
+CG_API cg_status cg_workspace_size(cg_plan plan, size_t *bytes)
+{
+    if (!plan || !bytes) return fail(CG_EINVAL, "NULL argument");
+    *bytes = cgk::WS_HEADER + (size_t)plan->scratch_elems * sizeof(double);
+    return CG_OK;
+}
+
+CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps, void *workspace,
+                        void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
+    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(z_in) & 7) || (reinterpret_cast<uintptr_t>(z_out) & 7))
+        return fail(CG_EINVAL, "state buffers must be 8-byte aligned");
+    const int64_t total = plan->offsets.back();
+    const size_t nbytes = (size_t)total * sizeof(double);
+    if (z_in != z_out) {
+        const char *a0 = reinterpret_cast<const char *>(z_in), *b0 = reinterpret_cast<const char *>(z_out);
+        if (a0 < b0 + nbytes && b0 < a0 + nbytes) return fail(CG_EINVAL, "z_in and z_out partially overlap");
+    }
+    cg_status st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    if (n_steps == 0) {
+        if (z_in != z_out) {
+            e = cudaMemcpyAsync(z_out, z_in, nbytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        return CG_OK;
+    }
+
+    RunArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = plan->d_inst;
+    a.n_inst = (int32_t)plan->inst.size();
+    a.n_tiles = plan->n_tiles;
+    a.bc = plan->bc;
+    a.rows = plan->rows;
+    a.z_in = z_in;
+    a.z_out = z_out;
+    a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
+    a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
+    a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
+    const bool alias_single_stage = (plan->ns == 1) && (z_in == z_out);
+    a.parity = alias_single_stage ? 1 : (int32_t)((n_steps - 1) & 1);
+    a.timeout_ns = plan->timeout_ns;
+    std::memcpy(a.cacc, plan->cacc, sizeof a.cacc);
+    std::memcpy(a.cy, plan->cy, sizeof a.cy);
+    std::memcpy(a.mp, plan->mp, sizeof a.mp);
+    const int64_t G = n_steps * plan->ns;
+    void *args[] = {&a};
+
+    if (plan->flags & CG_FLAG_PER_STAGE_LAUNCH) {
+        const int wpb = plan->threads / 32;
+        const int grid = (plan->n_tiles + wpb - 1) / wpb;
+        a.persistent = 0;
+        for (int64_t g = 0; g < G; ++g) {
+            a.g_begin = g;
+            a.g_end = g + 1;
+            e = cudaLaunchKernel(plan->kernel, dim3(grid), dim3(plan->threads), args, 0, s);
+            if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+        }
+    } else {
+        a.persistent = 1;
+        a.g_begin = 0;
+        a.g_end = G;
+        a.nblocks_expect = (uint32_t)plan->nblocks;
+        a.stuck_barrier = (plan->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3(plan->nblocks);
+        cfg.blockDim = dim3(plan->threads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, plan->kernel, args);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+    }
+    if (alias_single_stage && (n_steps & 1)) {
+        // odd number of single-stage steps in place: the last result sits in
+        // the scratch copy of each instance
+        for (size_t k = 0; k < plan->inst.size(); ++k) {
+            const Inst &I = plan->inst[k];
+            e = cudaMemcpyAsync(z_out + I.off, a.ws + I.ws_off,
+                                sizeof(double) * (size_t)plan->nv * I.nx * I.ny, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
+        }
+    }
+    return CG_OK;
+}
+
+CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags)
+{
+    if (!plan || !workspace || !flags) return fail(CG_EINVAL, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    uint32_t v = 0;
+    e = cudaMemcpy(&v, reinterpret_cast<const char *>(workspace) + cgk::WS_STATUS_OFF, sizeof v,
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    *flags = v;
+    if (v & CG_DEV_TIMEOUT) return fail(CG_ETIMEOUT, "a device-side wait gave up (status 0x%x)", v);
+    if (v & CG_DEV_NONFINITE) return fail(CG_ENAN, "a non-finite value was written (status 0x%x)", v);
+    return CG_OK;
+}
+
+CG_API const char *cg_last_error(void)
+{
+    return g_err.c_str();
+}
+
+CG_API int32_t cg_n_fields(int32_t model)
+{
+    return n_fields(model);
+}
+
+CG_API int32_t cg_n_params(int32_t model)
+{
+    return n_params(model);
+}
+
+CG_API cg_status cg_default_params(int32_t model, double *out)
+{
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    if (n_params(model) < 0) return fail(CG_EINVAL, "unknown model %d", model);
+    default_params(model, out);
+    return CG_OK;
+}
+
+CG_API int32_t cg_abi_version(void)
+{
+    return CG_ABI_VERSION;
+}

@@ -1,0 +1,66 @@
+// Internal definitions shared by the host library and the kernels of
+// libcardiac_gb300.so.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cardiac_gb300.h"
+
+namespace cgk {
+
+constexpr int MAXF = 4;     // fields per cell (BOCF: u, v, w, s)
+constexpr int NMP = 48;     // model constants shared by all instances of a plan
+
+// One grid instance, resident in a plan-owned device table.  Coefficients
+// carry D/dx^2 and the stencil weights; the centre weight is folded into the
+// model constants so that a cell's right-hand side is one FMA chain.
+struct Inst {
+    int32_t nx, ny;
+    int32_t tiles_x, tiles_y;
+    int32_t tile_begin;      // global tile id of this instance's first tile
+    int32_t vec_ok;          // nx even and packed offset even: rows start 16-byte aligned
+    int64_t off;             // element offset of the instance in packed state buffers
+    int64_t ws_off;          // element offset of the instance's scratch block in the workspace
+    double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights
+    double mi[4];            // instance-dependent folds of centre weight and model constants
+};
+
+// Kernel argument block (passed by value).
+struct RunArgs {
+    const Inst *inst;
+    int32_t n_inst, n_tiles;
+    int32_t bc, rows;            // ghost mode, rows per warp tile
+    const double *z_in;
+    double *z_out;
+    double *ws;                  // base of the per-instance scratch blocks
+    unsigned *sync;              // [0] barrier count, [1] barrier generation, [2..4] tile queues
+    uint32_t *status;            // device status word (CG_DEV_*)
+    int64_t g_begin, g_end;      // global stage range [g_begin, g_end) of this launch
+    int32_t parity;              // step k stores its result in z_out iff (k + parity) is even
+    int32_t persistent;          // 1: loop over stages with grid barriers; 0: one stage
+    uint32_t nblocks_expect;     // arrivals the grid barrier waits for
+    uint32_t stuck_barrier;      // testing knob: first barrier waits for one extra block
+    uint64_t timeout_ns;         // bound on a barrier wait
+    double cacc[4], cy[4];       // per-stage combine weights (b_s dt and a_{s+1,s} dt)
+    double mp[NMP];              // model constants (layout per model, see cg_stepper.cuh)
+};
+
+// Scratch block of one instance (doubles): zb | acc | Ya | Yb, each n_v planes.
+constexpr int SCRATCH_PLANES = 4;
+
+// Workspace header (bytes): status word and sync counters.
+constexpr size_t WS_HEADER = 256;
+constexpr size_t WS_STATUS_OFF = 0;
+constexpr size_t WS_SYNC_OFF = 64;
+constexpr int SYNC_WORDS = 8;
+
+enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION };
+
+// Kernel lookup, one function per model translation unit.  Returns nullptr
+// for an unsupported combination.
+const void *fwd_kernel_fhn(int stencil, int scheme, int cx);
+const void *fwd_kernel_bocf(int stencil, int scheme, int cx);
+const void *fwd_kernel_diff(int stencil, int scheme, int cx);
+
+}  // namespace cgk

@@ -1,0 +1,509 @@
+// Fused explicit stage kernel for dz/dt = D L z + N[z] (Eq. rdeqn, Sect. 2-3).
+//
+// One warp owns a tile of 32*CX columns x `rows` rows of one instance.  It
+// sweeps the rows from bottom to top keeping a three-row register window of
+// every diffusive field; west/east neighbours come from the neighbouring
+// lanes by warp shuffles, the two columns just outside the tile are loaded by
+// lanes 0 and 31.  Ghost points (Fig. 1) are resolved in the load indices:
+// column -1 reads column 1 (MIRROR) or 0 (CLAMP), column nx reads nx-2 or
+// nx-1, and likewise for rows, so no branch touches the arithmetic.
+//
+// Each cell of each stage costs one FMA chain: the model's local terms with
+// the stencil's centre weight folded in, then the off-centre stencil sums,
+// then the Runge-Kutta combine (two FMAs per field, one in the last stage).
+// The FP64 pipe is the binding resource on GB300, so every non-FP64 piece of
+// work (index arithmetic, clamps of the smoothed steps, NaN checks) is done
+// with integer instructions.
+//
+// Launch modes: persistent (one cooperative launch runs all stages of all
+// steps; tiles are handed out by an atomic queue per stage and stages are
+// separated by a bounded grid barrier) or one launch per stage (static tile
+// assignment, no waiting).
+#pragma once
+
+#include "cg_internal.h"
+
+namespace cgk {
+
+#define CG_FULL 0xffffffffu
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t nonfinite_bit(double v)
+{
+    return (uint32_t)((((unsigned long long)__double_as_longlong(v)) >> 52 & 0x7ffull) == 0x7ffull);
+}
+
+// Clamp to [0, 1] on the integer pipe: non-negative doubles order like their
+// bit patterns, and every negative double has the sign bit set.
+__device__ __forceinline__ double clamp01_int(double t)
+{
+    long long b = __double_as_longlong(t);
+    b = b < 0 ? 0 : b;
+    b = b > 0x3FF0000000000000ll ? 0x3FF0000000000000ll : b;
+    return __longlong_as_double(b);
+}
+
+// Smoothed step H_k(u - theta) of Sect. 2 with t = k (u - theta) + 1/2
+// clamped to [0, 1]; H = t^2 (3 - 2 t).  c = 1/2 - k theta.
+__device__ __forceinline__ double smooth_step(double u, double k, double c)
+{
+    double t = clamp01_int(fma(k, u, c));
+    return (t * t) * fma(-2.0, t, 3.0);
+}
+
+// Bounded grid barrier.  Thread 0 of each block arrives on a counter; the
+// last arrival resets it and bumps the generation word.  The others spin on
+// the generation with a time limit; on expiry the block records
+// CG_DEV_TIMEOUT and every thread of the block returns false.
+static __device__ __noinline__ bool grid_barrier(unsigned *sync, uint32_t *status, uint64_t timeout_ns,
+                                          uint32_t expect)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned *count = sync;
+        unsigned *gen = sync + 1;
+        const unsigned g0 = ld_acquire_u32(gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == expect) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = global_timer_ns();
+            const uint64_t max_iter = (timeout_ns >> 5) + (1ull << 20);
+            uint64_t it = 0;
+            while (ld_acquire_u32(gen) == g0) {
+                __nanosleep(64);
+                if ((++it & 63) == 0) {
+                    if (global_timer_ns() - t0 > timeout_ns || it > max_iter) {
+                        ok = 0;
+                        atomicOr(status, CG_DEV_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ models
+
+template <int M> struct Model;
+
+// FitzHugh-Nagumo, Eq. (fhn): both fields diffusive.
+//   F_u = (1 + wc_u) u - v - u^3 + stencil_u
+//   F_v = eps u + (wc_v - eps a1) v - eps a0 + stencil_v
+template <> struct Model<MODEL_FHN> {
+    static constexpr int NV = 2, ND = 2;
+    struct Coef { double A_u, B_v; };
+    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.mi[1]}; }
+    // mp[0] = eps, mp[1] = -eps a0 ; Coef holds instance-dependent folds.
+    __device__ static void local(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV])
+    {
+        const double u = z[0], v = z[1];
+        const double p = u * u;
+        t[0] = fma(-p, u, fma(c.A_u, u, -v));
+        t[1] = fma(mp[0], u, fma(c.B_v, v, mp[1]));
+    }
+};
+
+// Pure diffusion (N = 0), one field: F = wc u + stencil.
+template <> struct Model<MODEL_DIFF> {
+    static constexpr int NV = 1, ND = 1;
+    struct Coef { double wc; };
+    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0]}; }
+    __device__ static void local(const Coef &c, const double *, const double (&z)[NV], double (&t)[NV])
+    {
+        t[0] = c.wc * z[0];
+    }
+};
+
+// Bueno-Orovio-Cherry-Fenton, Eq. (bochfe) with the currents J_fi, J_so,
+// J_si, the alpha/beta gate form and the u-dependent time constants of the
+// cited minimal model; every step is the cubic H_k.  Only u diffuses.
+// Constant layout of mp (filled by the host):
+enum {
+    BP_UO, BP_UU, BP_THV, BP_THW, BP_THVM, BP_THO,
+    BP_TV1M, BP_TV2M, BP_TVP, BP_TW1M, BP_TW2M, BP_KWM, BP_UWM, BP_TWP,
+    BP_TFI, BP_TO1, BP_TO2, BP_TSO1, BP_TSO2, BP_KSO, BP_USO,
+    BP_TS1, BP_TS2, BP_KS, BP_US, BP_TSI, BP_TWINF, BP_WINFSTAR, BP_K,
+    BP_NRAW,
+    // derived on the host
+    BD_CV = BP_NRAW,   // 1/2 - k thv
+    BD_CW,             // 1/2 - k thw
+    BD_CVM,            // 1/2 - k thvm
+    BD_CO,             // 1/2 - k tho
+    BD_DTV,            // tv2m - tv1m
+    BD_DTO,            // to2 - to1
+    BD_DTS,            // ts2 - ts1
+    BD_IFI,            // 1/tfi
+    BD_ISI,            // 1/tsi
+    BD_IVP,            // 1/tvp
+    BD_IWP,            // 1/twp
+    BD_IWINF,          // 1/twinf
+    BD_N
+};
+
+template <> struct Model<MODEL_BOCF> {
+    static constexpr int NV = 4, ND = 1;
+    struct Coef { double wc_u; };
+    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0]}; }
+    __device__ static void local(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV])
+    {
+        const double u = z[0], v = z[1], w = z[2], s = z[3];
+        const double k = mp[BP_K];
+        const double Hv = smooth_step(u, k, mp[BD_CV]);
+        const double Hw = smooth_step(u, k, mp[BD_CW]);
+        const double Hvm = smooth_step(u, k, mp[BD_CVM]);
+        const double Ho = smooth_step(u, k, mp[BD_CO]);
+        const double tau_vm = fma(Hvm, mp[BD_DTV], mp[BP_TV1M]);
+        const double v_inf = 1.0 - Hvm;
+        const double tau_wm = mp[BP_TW1M] + (mp[BP_TW2M] - mp[BP_TW1M]) *
+                              (1.0 + tanh(mp[BP_KWM] * (u - mp[BP_UWM]))) * 0.5;
+        const double q = fma(-u, mp[BD_IWINF], 1.0);
+        const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
+        const double tau_o = fma(Ho, mp[BD_DTO], mp[BP_TO1]);
+        const double tau_so = mp[BP_TSO1] + (mp[BP_TSO2] - mp[BP_TSO1]) *
+                              (1.0 + tanh(mp[BP_KSO] * (u - mp[BP_USO]))) * 0.5;
+        const double tau_s = fma(Hw, mp[BD_DTS], mp[BP_TS1]);
+        const double J_fi = -v * Hv * (u - mp[BP_THV]) * (mp[BP_UU] - u) * mp[BD_IFI];
+        const double J_so = (u - mp[BP_UO]) * (1.0 - Hw) / tau_o + Hw / tau_so;
+        const double J_si = -Hw * w * s * mp[BD_ISI];
+        t[0] = fma(c.wc_u, u, -(J_fi + J_so + J_si));
+        t[1] = (1.0 - Hv) * (v_inf - v) / tau_vm - Hv * v * mp[BD_IVP];
+        t[2] = (1.0 - Hw) * (w_inf - w) / tau_wm - Hw * w * mp[BD_IWP];
+        t[3] = ((1.0 + tanh(mp[BP_KS] * (u - mp[BP_US]))) * 0.5 - s) / tau_s;
+    }
+};
+
+// ------------------------------------------------------------- index maps
+
+__device__ __forceinline__ int map_lo(int bc) { return bc == CG_BC_MIRROR ? 1 : 0; }
+
+// Column/row index with ghost resolution: i == -1 and i == n are the ghost
+// points of Fig. 1; i > n is outside every stored cell's stencil and is
+// clamped only to stay in bounds.
+__device__ __forceinline__ int map_idx(int i, int n, int bc)
+{
+    if (i < 0) return map_lo(bc);
+    if (i == n) return bc == CG_BC_MIRROR ? n - 2 : n - 1;
+    return i < n ? i : n - 1;
+}
+
+// ------------------------------------------------------------ tile worker
+
+template <int M, int ST, int NS, int CX>
+struct Stepper {
+    using MD = Model<M>;
+    static constexpr int NV = MD::NV, ND = MD::ND;
+
+    __device__ static inline void load_row(const double *plane, int nx, int yrow, const int (&cx)[CX],
+                                           int hx, bool vec, bool want_halo, double (&v)[CX], double &h)
+    {
+        const double *rp = plane + (int64_t)yrow * nx;
+        if (CX == 2 && vec) {
+            const double2 d = __ldcg(reinterpret_cast<const double2 *>(rp + cx[0]));
+            v[0] = d.x;
+            v[CX - 1] = d.y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < CX; ++c) v[c] = __ldcg(rp + cx[c]);
+        }
+        if (want_halo) h = __ldcg(rp + hx);
+    }
+
+    // Process stage s of step `step` on local tile lt of instance I.
+    __device__ __forceinline__ static uint32_t tile(const RunArgs &a, const Inst &I, const double *mp, int lt, int s,
+                                    int64_t step, int lane)
+    {
+        const int nx = I.nx, ny = I.ny, bc = a.bc;
+        const int tx = lt % I.tiles_x, ty = lt / I.tiles_x;
+        const int xt = tx * 32 * CX;
+        const int y0 = ty * a.rows;
+        const int nrows = min(a.rows, ny - y0);
+        const int64_t plane = (int64_t)nx * ny;
+
+        double *blk = a.ws + I.ws_off;
+        double *zb = blk;
+        double *acc = blk + NV * plane;
+        double *Ya = blk + 2 * NV * plane;
+        double *Yb = blk + 3 * NV * plane;
+        const double *zin = a.z_in + I.off;
+        double *zout = a.z_out + I.off;
+        const double *src = (step == 0) ? zin : ((((step - 1) + a.parity) & 1) == 0 ? zout : zb);
+        double *dst = (((step + a.parity) & 1) == 0) ? zout : zb;
+        const double *Yin = (s == 0) ? src : ((s & 1) ? Ya : Yb);
+        double *Ynext = (s & 1) ? Yb : Ya;
+        const bool last = (s == NS - 1);
+        const double ca = a.cacc[s];
+        const double cyv = last ? 0.0 : a.cy[s];
+
+        // columns of this lane's cells and of the tile's halo columns
+        const int x0 = xt + CX * lane;
+        int cx[CX];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) cx[c] = map_idx(x0 + c, nx, bc);
+        const bool want_halo = (lane == 0) || (lane == 31);
+        const int hx = map_idx(lane == 0 ? xt - 1 : xt + 32 * CX, nx, bc);
+        const bool full = (x0 + CX - 1) < nx;     // every cell of this lane is stored
+        const bool aligned_base = I.vec_ok != 0;
+        auto vec_for = [&](const void *p) {
+            return CX == 2 && aligned_base && full && ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
+        };
+        const bool vin = vec_for(Yin), vsrc = vec_for(src), vacc = vec_for(acc);
+        const bool vdst = vec_for(dst), vyn = vec_for(Ynext);
+
+        // stencil weights of the diffusive fields
+        double wx[ND], wy[ND], wd[ND];
+#pragma unroll
+        for (int f = 0; f < ND; ++f) {
+            wx[f] = I.wx[f];
+            wy[f] = I.wy[f];
+            wd[f] = I.wd[f];
+        }
+        const typename MD::Coef coef = MD::coef(I);
+
+        double lo[ND][CX], mid[ND][CX], hi[ND][CX];
+        double hlo[ND], hmid[ND], hhi[ND];
+#pragma unroll
+        for (int f = 0; f < ND; ++f) {
+            hlo[f] = hmid[f] = hhi[f] = 0.0;
+            load_row(Yin + f * plane, nx, map_idx(y0 - 1, ny, bc), cx, hx, vin, want_halo, lo[f], hlo[f]);
+            load_row(Yin + f * plane, nx, y0, cx, hx, vin, want_halo, mid[f], hmid[f]);
+        }
+
+        uint32_t bad = 0;
+        for (int r = 0; r < nrows; ++r) {
+            const int y = y0 + r;
+            const int yn = map_idx(y + 1, ny, bc);
+#pragma unroll
+            for (int f = 0; f < ND; ++f)
+                load_row(Yin + f * plane, nx, yn, cx, hx, vin, want_halo, hi[f], hhi[f]);
+
+            // centre values of every field
+            double zc[CX][NV];
+#pragma unroll
+            for (int f = 0; f < NV; ++f) {
+                if (f < ND) {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) zc[c][f] = mid[f < ND ? f : 0][c];
+                } else {
+                    double v[CX], dummy;
+                    load_row(Yin + f * plane, nx, y, cx, hx, vin, false, v, dummy);
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) zc[c][f] = v[c];
+                }
+            }
+
+            // local terms (centre weight folded in)
+            double F[CX][NV];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                double t[NV];
+                MD::local(coef, mp, zc[c], t);
+#pragma unroll
+                for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+            }
+
+            // off-centre stencil sums of the diffusive fields
+#pragma unroll
+            for (int f = 0; f < ND; ++f) {
+                double up = __shfl_up_sync(CG_FULL, mid[f][CX - 1], 1);
+                double dn = __shfl_down_sync(CG_FULL, mid[f][0], 1);
+                if (lane == 0) up = hmid[f];
+                if (lane == 31) dn = hmid[f];
+                double V[CX];
+#pragma unroll
+                for (int c = 0; c < CX; ++c) V[c] = lo[f][c] + hi[f][c];
+                double Vl = 0.0, Vr = 0.0;
+                if (ST == CG_STENCIL9) {
+                    const double Vh = hlo[f] + hhi[f];
+                    Vl = __shfl_up_sync(CG_FULL, V[CX - 1], 1);
+                    Vr = __shfl_down_sync(CG_FULL, V[0], 1);
+                    if (lane == 0) Vl = Vh;
+                    if (lane == 31) Vr = Vh;
+                }
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    const double W = (c == 0) ? up : mid[f][c - 1];
+                    const double E = (c == CX - 1) ? dn : mid[f][c + 1];
+                    double acc_f = F[c][f];
+                    if (ST == CG_STENCIL9) {
+                        const double VW = (c == 0) ? Vl : V[c - 1];
+                        const double VE = (c == CX - 1) ? Vr : V[c + 1];
+                        acc_f = fma(wd[f], VW + VE, acc_f);
+                    }
+                    acc_f = fma(wy[f], V[c], acc_f);
+                    acc_f = fma(wx[f], W + E, acc_f);
+                    F[c][f] = acc_f;
+                }
+            }
+
+            // Runge-Kutta combine and stores
+            const int64_t ro = (int64_t)y * nx;
+#pragma unroll
+            for (int f = 0; f < NV; ++f) {
+                double base[CX];
+                if (s == 0) {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) base[c] = zc[c][f];
+                } else {
+                    double dummy;
+                    load_row(acc + f * plane, nx, y, cx, hx, vacc, false, base, dummy);
+                }
+                double outv[CX];
+#pragma unroll
+                for (int c = 0; c < CX; ++c) outv[c] = fma(ca, F[c][f], base[c]);
+                double *op = (last ? dst : acc) + f * plane + ro;
+                const bool vo = last ? vdst : vacc;
+                if (CX == 2 && vo) {
+                    __stcg(reinterpret_cast<double2 *>(op + x0), make_double2(outv[0], outv[CX - 1]));
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c)
+                        if (x0 + c < nx) __stcg(op + x0 + c, outv[c]);
+                }
+                if (last) {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c)
+                        if (x0 + c < nx) bad |= nonfinite_bit(outv[c]);
+                } else {
+                    double zz[CX];
+                    if (s == 0) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c) zz[c] = zc[c][f];
+                    } else {
+                        double dummy;
+                        load_row(src + f * plane, nx, y, cx, hx, vsrc, false, zz, dummy);
+                    }
+                    double yv[CX];
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) yv[c] = fma(cyv, F[c][f], zz[c]);
+                    double *yp = Ynext + f * plane + ro;
+                    if (CX == 2 && vyn) {
+                        __stcg(reinterpret_cast<double2 *>(yp + x0), make_double2(yv[0], yv[CX - 1]));
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c)
+                            if (x0 + c < nx) __stcg(yp + x0 + c, yv[c]);
+                    }
+                }
+            }
+
+            // slide the window
+#pragma unroll
+            for (int f = 0; f < ND; ++f) {
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    lo[f][c] = mid[f][c];
+                    mid[f][c] = hi[f][c];
+                }
+                hlo[f] = hmid[f];
+                hmid[f] = hhi[f];
+            }
+        }
+        return bad;
+    }
+};
+
+template <int M, int ST, int NS, int CX>
+__global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
+{
+    using S = Stepper<M, ST, NS, CX>;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const double *mp = a.mp;
+    uint32_t bad = 0;
+
+    auto find_inst = [&](int t) -> int {
+        int lo = 0, hi = a.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.inst[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+
+    if (!a.persistent) {
+        const int64_t g = a.g_begin;
+        const int s = (int)(g % NS);
+        const int64_t step = g / NS;
+        for (int t = blockIdx.x * nwarps + warp; t < a.n_tiles; t += gridDim.x * nwarps) {
+            const int i = find_inst(t);
+            const Inst &I = a.inst[i];
+            bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+        }
+    } else {
+        bool first_barrier = true;
+        for (int64_t g = a.g_begin; g < a.g_end; ++g) {
+            const int s = (int)(g % NS);
+            const int64_t step = g / NS;
+            unsigned *q = a.sync + 2 + (int)(g % 3);
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.sync + 2 + (int)((g + 1) % 3), 0u);
+            int t = 0;
+            if (lane == 0) t = (int)atomicAdd(q, 1u);
+            t = __shfl_sync(CG_FULL, t, 0);
+            while (t < a.n_tiles) {
+                int tn = 0;
+                if (lane == 0) tn = (int)atomicAdd(q, 1u);
+                const int i = find_inst(t);
+                const Inst &I = a.inst[i];
+                bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+                t = __shfl_sync(CG_FULL, tn, 0);
+            }
+            if (g + 1 < a.g_end) {
+                const uint32_t expect = a.nblocks_expect + ((first_barrier && a.stuck_barrier) ? 1u : 0u);
+                first_barrier = false;
+                if (!grid_barrier(a.sync, a.status, a.timeout_ns, expect)) return;
+            }
+        }
+    }
+    bad = __any_sync(CG_FULL, bad != 0);
+    if (lane == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+}
+
+// Kernel table for one model: [stencil][scheme][cx-1].
+template <int M>
+inline const void *pick_fwd_kernel(int stencil, int scheme, int cx)
+{
+    if (cx != 1 && cx != 2) return nullptr;
+#define CG_K(ST, NS, CXV) reinterpret_cast<const void *>(&k_stage<M, ST, NS, CXV>)
+#define CG_SCH(ST, CXV)                                  \
+    switch (scheme) {                                    \
+    case CG_EULER: return CG_K(ST, 1, CXV);             \
+    case CG_HEUN: return CG_K(ST, 2, CXV);              \
+    case CG_RK4: return CG_K(ST, 4, CXV);               \
+    default: return nullptr;                             \
+    }
+    if (stencil == CG_STENCIL5) {
+        if (cx == 1) { CG_SCH(CG_STENCIL5, 1) } else { CG_SCH(CG_STENCIL5, 2) }
+    } else if (stencil == CG_STENCIL9) {
+        if (cx == 1) { CG_SCH(CG_STENCIL9, 1) } else { CG_SCH(CG_STENCIL9, 2) }
+    }
+#undef CG_SCH
+#undef CG_K
+    return nullptr;
+}
+
+}  // namespace cgk

@@ -1,0 +1,78 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point the public header declares, validates problems before any
+device call, and carries the same model constants as the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1309_1720_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(cg_[a-z0-9_]+)\s*\(",
+                                src, flags=re.M)
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_abi_version(L):
+    assert L.cg_abi_version() == 1
+
+
+def test_default_params_match_oracle(L):
+    import oracle as O
+    from paper_1309_1720_gb300 import api
+    for m_abi, m_orc in [(api.FHN, O.FHN), (api.BOCF, O.BOCF)]:
+        assert api.n_fields(m_abi) == O.n_fields(m_orc)
+        assert np.array_equal(np.array(api.default_params(m_abi)), O.default_params(m_orc))
+
+
+def _create(prob):
+    from paper_1309_1720_gb300 import _lib
+    c = prob.to_c()
+    h = ctypes.c_void_p()
+    st = _lib.lib().cg_plan_create(ctypes.byref(c), ctypes.byref(h))
+    return st, _lib.lib().cg_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(nx=1), 1), (dict(ny=0), 1), (dict(dx=0.0), 1), (dict(dt=-1.0), 1),
+    (dict(stencil=7), 1), (dict(bc=5), 1), (dict(scheme=9), 1), (dict(model=42), 1),
+    (dict(model=2), 7),                     # Karma: constants not in the paper
+    (dict(dt=3e-4), 4),                     # FE bound for FHN at dx=0.04 is 2.67e-4
+    (dict(scheme=2, dt=5.6e-4), 4),         # RK4 5-point bound 3.71e-4
+    (dict(stencil=1, alpha_d=0.4), 1),
+    (dict(params=[0.05, 1.5]), 1),
+])
+def test_validation_errors(L, kw, status):
+    from paper_1309_1720_gb300 import Problem
+    st, msg = _create(Problem(**kw))
+    assert st == status, msg
+    assert msg
+
+
+def test_bocf_gate_diffusion_rejected(L):
+    from paper_1309_1720_gb300 import Problem, BOCF
+    st, msg = _create(Problem(model=BOCF, dx=0.03, dt=0.05, D=(1e-3, 1e-3)))
+    assert st == 7 and "diffuse" in msg
