@@ -22,6 +22,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -228,6 +230,54 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t,
                                            "steps_timed": steps, "note": "rate of 500 of the 5000 steps"}
     plan.close()
+
+    # 256 uneven instances (64..512, seed 1), 5-point RK4: one persistent
+    # launch replayed from a CUDA graph vs 256 sequential single-instance runs
+    steps = 200
+    sizes, states, dus = I.batch_workload(n_inst=256, seed=1)
+    probs = [api.Problem(model=api.FHN, nx=int(n), ny=int(n), dx=0.04, D=(float(d), 1.5),
+                         scheme=api.RK4, dt=2.5e-4) for n, d in zip(sizes, dus)]
+    cells = int(np.sum(sizes.astype(np.int64) ** 2))
+    bp = plan_cls(probs)
+    zin = bp.pack(states)
+    zout = torch.empty_like(zin)
+    bp.run(zin, steps, out=zout)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp.run(zin, steps, out=zout, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1) / 1e3)
+    bp.status()
+    seq_plans = [plan_cls(p) for p in probs]
+    parts_in = bp.unpack(zin)
+    outs = [torch.empty_like(x) for x in parts_in]
+    for sp, zi, zo in zip(seq_plans, parts_in, outs):
+        sp.run(zi, steps, out=zo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for sp, zi, zo in zip(seq_plans, parts_in, outs):
+        sp.run(zi, steps, out=zo)
+    e1.record()
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / 1e3
+    same = all(torch.equal(a, b) for a, b in zip(outs, bp.unpack(zout)))
+    rows["batch-256x(64..512)^2-5pt-rk4"] = {
+        "gcups_batched": cells * steps / min(tb) / 1e9, "gcups_sequential": cells * steps / ts / 1e9,
+        "speedup": ts / min(tb), "cells": cells, "steps_timed": steps, "bitwise_equal_to_sequential": same,
+        "note": "rate of 200 of the 2000 steps; batched = one graph-replayed persistent launch"}
+    for sp in seq_plans:
+        sp.close()
+    bp.close()
     return rows
 
 

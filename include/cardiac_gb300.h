@@ -105,6 +105,10 @@ typedef struct cg_tuning {
     int32_t rows;          /* rows per warp tile, >= 1 */
     int32_t threads;       /* threads per block: 128, 256 or 512 */
     int32_t blocks_per_sm; /* persistent blocks per SM, >= 1 (capped by occupancy) */
+    int32_t schedule;      /* 0: static (equal cells per block, equal strip-rows per warp,
+                              computed at plan creation); 1: atomic tile queue per stage
+                              (tiles of 32*cells_x columns by `rows` rows, largest
+                              instances first) */
 } cg_tuning;
 
 typedef struct cg_plan_s *cg_plan;
@@ -173,6 +177,20 @@ int32_t cg_n_params(int32_t model);
  * (host memory).  FHN: Sect. 2 values; BOCF: the epicardial set of the
  * model the paper cites, then k = 28.4 for H_k. */
 cg_status cg_default_params(int32_t model, double *out);
+
+/* Host-only preview of the static schedule that plans use (no device
+ * needed): the cells of instances 0..n_inst-1 (in the given order, row-major
+ * inside each) are split into n_blocks equal ranges and each range into
+ * warps_per_block pieces of equal strip-rows, strips being 32*cells_x
+ * columns wide.  Writes *n_segs segments of 10 int32 each to segs_out (when
+ * not NULL and segs_cap allows): {inst, x0, y0, y1, mrow_a, ma0, ma1,
+ * mrow_b, mb0, mb1}, meaning columns [x0, x0 + 32*cells_x) of rows y0..y1,
+ * except that row mrow_a keeps only columns [ma0, ma1) and row mrow_b only
+ * [mb0, mb1); and n_blocks*warps_per_block + 1 prefix offsets to
+ * warp_seg_out (warp w owns segments [warp_seg_out[w], warp_seg_out[w+1])). */
+cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
+                             int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
+                             int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs);
 
 /* CG_ABI_VERSION of the loaded library. */
 int32_t cg_abi_version(void);

@@ -32,7 +32,8 @@ enum {
  * running 8 independent dependency chains of `op` for `iters` iterations,
  * and write the number of operations per second to *ops_per_s and the kernel
  * time to *seconds (either may be NULL).  iters <= 0 picks a count that runs
- * for about 50 ms on GB300.  Synchronous. */
+ * for about 100 ms on GB300 (after an untimed run half as long, so that the
+ * clocks have ramped).  Synchronous. */
 cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per_s, double *seconds);
 
 #ifdef __cplusplus

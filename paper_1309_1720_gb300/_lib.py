@@ -33,7 +33,8 @@ class CProblem(ctypes.Structure):
 class CTuning(ctypes.Structure):
     """Mirror of ``cg_tuning``."""
     _fields_ = [("cells_x", ctypes.c_int32), ("rows", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -59,6 +60,10 @@ _SIGS = {
     "cg_n_params": (ctypes.c_int32, [ctypes.c_int32]),
     "cg_default_params": (ctypes.c_int, [ctypes.c_int32, c_dp]),
     "cg_abi_version": (ctypes.c_int32, []),
+    "cg_static_schedule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     "cg_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
 }

@@ -114,7 +114,8 @@ class Plan:
         tun = None
         if tuning:
             tun = CTuning(int(tuning.get("cells_x", 0)), int(tuning.get("rows", 0)),
-                          int(tuning.get("threads", 0)), int(tuning.get("blocks_per_sm", 0)))
+                          int(tuning.get("threads", 0)), int(tuning.get("blocks_per_sm", 0)),
+                          int(tuning.get("schedule", 0)))
         h = ctypes.c_void_p()
         if single:
             st = L.cg_plan_create_tuned(cprobs, ctypes.byref(tun) if tun else None, ctypes.byref(h))

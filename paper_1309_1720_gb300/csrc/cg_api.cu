@@ -105,8 +105,13 @@ struct cg_plan_s {
     std::vector<int64_t> offsets;    // packed offsets in user order (n_inst + 1)
     std::vector<int32_t> order;      // user index -> tile-order index
     Inst *d_inst = nullptr;
+    std::vector<cgk::Seg> segs;      // static schedule
+    std::vector<int32_t> warp_seg;
+    cgk::Seg *d_segs = nullptr;
+    int32_t *d_warp_seg = nullptr;
+    int32_t sched = cgk::SCHED_STATIC;
     int32_t n_tiles = 0;
-    int32_t cx = 2, rows = 4, threads = 256, bpsm = 1;
+    int32_t cx = 2, rows = 4, threads = 512, bpsm = 1;
     int64_t scratch_elems = 0;
     double mp[cgk::NMP] = {};
     double cacc[4] = {}, cy[4] = {};
@@ -253,6 +258,80 @@ bool same_config(const cg_problem &a, const cg_problem &b)
     return true;
 }
 
+// Static schedule: the cells of all instances (in plan order, row-major
+// inside an instance) are cut into G equal ranges, one per block; a block's
+// range becomes column strips of 32*cx cells by row ranges, and those are
+// cut into NW pieces with equal numbers of strip-rows, one per warp.  Every
+// SM therefore gets the same FP64 work per stage, and so does each of its
+// warps (to within one row).
+void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int cx, int G, int NW,
+                     std::vector<cgk::Seg> &segs, std::vector<int32_t> &warp_seg)
+{
+    const int n = (int)nxs.size();
+    std::vector<int64_t> cstart(n + 1, 0);
+    for (int k = 0; k < n; ++k) cstart[k + 1] = cstart[k] + (int64_t)nxs[k] * nys[k];
+    const int64_t N = cstart[n];
+    const int tw = 32 * cx;
+    segs.clear();
+    warp_seg.assign((size_t)G * NW + 1, 0);
+    int k0 = 0;
+    for (int b = 0; b < G; ++b) {
+        const int64_t c0 = N * b / G, c1 = N * (b + 1) / G;
+        std::vector<cgk::Seg> bs;
+        while (k0 < n && cstart[k0 + 1] <= c0) ++k0;
+        for (int k = k0; k < n && cstart[k] < c1; ++k) {
+            const int64_t l0 = std::max(c0, cstart[k]) - cstart[k];
+            const int64_t l1 = std::min(c1, cstart[k + 1]) - cstart[k];
+            if (l0 >= l1) continue;
+            const int nx = nxs[k];
+            const int ya = (int)(l0 / nx), yb = (int)((l1 - 1) / nx);
+            const int fa0 = (int)(l0 % nx), fa1 = (ya == yb) ? (int)((l1 - 1) % nx) + 1 : nx;
+            const int fb0 = 0, fb1 = (int)((l1 - 1) % nx) + 1;
+            for (int x0 = 0; x0 < nx; x0 += tw) {
+                const int x1 = std::min(nx, x0 + tw);
+                const bool in_a = x1 > fa0 && x0 < fa1;
+                const bool in_b = (yb > ya) ? (x1 > fb0 && x0 < fb1) : in_a;
+                int r0 = in_a ? ya : ya + 1, r1 = in_b ? yb : yb - 1;
+                if (ya == yb) {
+                    if (!in_a) continue;
+                    r0 = r1 = ya;
+                }
+                if (r0 > r1) continue;
+                cgk::Seg sg;
+                sg.inst = k; sg.x0 = x0; sg.y0 = r0; sg.y1 = r1;
+                sg.mrow_a = ya; sg.ma0 = fa0; sg.ma1 = fa1;
+                sg.mrow_b = (yb > ya) ? yb : -1; sg.mb0 = fb0; sg.mb1 = fb1;
+                bs.push_back(sg);
+            }
+        }
+        int64_t total = 0;
+        for (const auto &sg : bs) total += sg.y1 - sg.y0 + 1;
+        // cut the block's strip-rows into NW consecutive shares
+        size_t si = 0;
+        int cur = bs.empty() ? 0 : bs[0].y0;     // next unassigned row of bs[si]
+        int64_t pos = 0;
+        for (int w = 0; w < NW; ++w) {
+            warp_seg[(size_t)b * NW + w] = (int32_t)segs.size();
+            const int64_t end = total * (w + 1) / NW;
+            while (pos < end && si < bs.size()) {
+                cgk::Seg sg = bs[si];
+                const int64_t avail = sg.y1 - cur + 1;
+                const int64_t take = std::min<int64_t>(avail, end - pos);
+                sg.y0 = cur;
+                sg.y1 = (int)(cur + take - 1);
+                segs.push_back(sg);
+                pos += take;
+                cur += (int)take;
+                if (cur > bs[si].y1) {
+                    ++si;
+                    if (si < bs.size()) cur = bs[si].y0;
+                }
+            }
+        }
+    }
+    warp_seg[(size_t)G * NW] = (int32_t)segs.size();
+}
+
 cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tune, cg_plan *out)
 {
     if (!out) return fail(CG_EINVAL, "out is NULL");
@@ -284,13 +363,19 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     for (int i = 0; i < n_inst; ++i) max_n = std::max<int64_t>(max_n, probs[i].nx);
     P->cx = (max_n >= 64) ? 2 : 1;
     P->rows = 4;
-    P->threads = 256;
-    P->bpsm = 2;
+    P->threads = 512;
+    P->bpsm = 1;
+    P->sched = cgk::SCHED_STATIC;
     if (tune) {
         if (tune->cells_x) P->cx = tune->cells_x;
         if (tune->rows) P->rows = tune->rows;
         if (tune->threads) P->threads = tune->threads;
         if (tune->blocks_per_sm) P->bpsm = tune->blocks_per_sm;
+        P->sched = tune->schedule;
+    }
+    if (P->sched != cgk::SCHED_STATIC && P->sched != cgk::SCHED_QUEUE) {
+        delete P;
+        return fail(CG_EINVAL, "tuning.schedule must be 0 (static) or 1 (queue)");
     }
     if ((P->cx != 1 && P->cx != 2) || P->rows < 1 || P->rows > 4096 ||
         (P->threads != 128 && P->threads != 256 && P->threads != 512) || P->bpsm < 1 || P->bpsm > 8) {
@@ -367,15 +452,29 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         delete P;
         return fail(CG_EUNSUPPORTED, "kernel cannot run with %d threads per block", P->threads);
     }
+    if (e == cudaSuccess) {
+        P->nblocks = P->num_sms * std::min(P->bpsm, occ);
+        std::vector<int32_t> nxs, nys;
+        for (const Inst &I : P->inst) { nxs.push_back(I.nx); nys.push_back(I.ny); }
+        static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_inst, sizeof(Inst) * n_inst);
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_inst, P->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_segs, sizeof(cgk::Seg) * std::max<size_t>(1, P->segs.size()));
+    if (e == cudaSuccess && !P->segs.empty())
+        e = cudaMemcpy(P->d_segs, P->segs.data(), sizeof(cgk::Seg) * P->segs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_warp_seg, sizeof(int32_t) * P->warp_seg.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_warp_seg, P->warp_seg.data(), sizeof(int32_t) * P->warp_seg.size(),
+                       cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (P->d_inst) cudaFree(P->d_inst);
+        if (P->d_segs) cudaFree(P->d_segs);
+        if (P->d_warp_seg) cudaFree(P->d_warp_seg);
         delete P;
         return cuda_fail(e, "plan creation");
     }
-    P->nblocks = P->num_sms * std::min(P->bpsm, occ);
     *out = P;
     g_err.clear();
     return CG_OK;
@@ -426,6 +525,8 @@ CG_API cg_status cg_plan_destroy(cg_plan plan)
 {
     if (!plan) return CG_OK;
     if (plan->d_inst) cudaFree(plan->d_inst);
+    if (plan->d_segs) cudaFree(plan->d_segs);
+    if (plan->d_warp_seg) cudaFree(plan->d_warp_seg);
     delete plan;
     return CG_OK;
 }
@@ -470,6 +571,9 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     RunArgs a;
     std::memset(&a, 0, sizeof a);
     a.inst = plan->d_inst;
+    a.segs = plan->d_segs;
+    a.warp_seg = plan->d_warp_seg;
+    a.sched = plan->sched;
     a.n_inst = (int32_t)plan->inst.size();
     a.n_tiles = plan->n_tiles;
     a.bc = plan->bc;
@@ -490,7 +594,7 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
 
     if (plan->flags & CG_FLAG_PER_STAGE_LAUNCH) {
         const int wpb = plan->threads / 32;
-        const int grid = (plan->n_tiles + wpb - 1) / wpb;
+        const int grid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
         a.persistent = 0;
         for (int64_t g = 0; g < G; ++g) {
             a.g_begin = g;
@@ -567,6 +671,29 @@ CG_API cg_status cg_default_params(int32_t model, double *out)
     if (!out) return fail(CG_EINVAL, "out is NULL");
     if (n_params(model) < 0) return fail(CG_EINVAL, "unknown model %d", model);
     default_params(model, out);
+    return CG_OK;
+}
+
+CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
+                                    int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
+                                    int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs)
+{
+    if (!nx || !ny || n_inst < 1 || (cells_x != 1 && cells_x != 2) || n_blocks < 1 || warps_per_block < 1 ||
+        !warp_seg_out || !n_segs)
+        return fail(CG_EINVAL, "bad schedule request");
+    std::vector<int32_t> nxs(nx, nx + n_inst), nys(ny, ny + n_inst);
+    for (int i = 0; i < n_inst; ++i)
+        if (nxs[i] < 1 || nys[i] < 1) return fail(CG_EINVAL, "instance %d has an empty grid", i);
+    std::vector<cgk::Seg> segs;
+    std::vector<int32_t> ws;
+    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws);
+    *n_segs = (int64_t)segs.size();
+    std::copy(ws.begin(), ws.end(), warp_seg_out);
+    if (segs_out) {
+        if ((int64_t)segs.size() > segs_cap) return fail(CG_EINVAL, "segs_cap too small (%lld needed)",
+                                                         (long long)segs.size());
+        std::memcpy(segs_out, segs.data(), sizeof(cgk::Seg) * segs.size());
+    }
     return CG_OK;
 }
 

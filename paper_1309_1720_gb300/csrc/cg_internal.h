@@ -26,9 +26,24 @@ struct Inst {
     double mi[4];            // instance-dependent folds of centre weight and model constants
 };
 
+// A warp's share of one stage under the static schedule: columns
+// [x0, x0 + 32*CX) of rows y0..y1 of instance `inst`.  Row mrow_a only owns
+// columns [ma0, ma1) and row mrow_b only [mb0, mb1) (the partial rows at the
+// ends of a block's cell range); -1 disables a mask.
+struct Seg {
+    int32_t inst, x0, y0, y1;
+    int32_t mrow_a, ma0, ma1;
+    int32_t mrow_b, mb0, mb1;
+};
+
+enum { SCHED_STATIC = 0, SCHED_QUEUE = 1 };
+
 // Kernel argument block (passed by value).
 struct RunArgs {
     const Inst *inst;
+    const Seg *segs;             // static schedule: segments of every warp
+    const int32_t *warp_seg;     // warp w of the grid owns segs[warp_seg[w] .. warp_seg[w+1])
+    int32_t sched;               // SCHED_STATIC or SCHED_QUEUE
     int32_t n_inst, n_tiles;
     int32_t bc, rows;            // ghost mode, rows per warp tile
     const double *z_in;

@@ -42,12 +42,12 @@ CG_API cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per
     const void *k = nullptr;
     int64_t def = 0;
     switch (op) {
-    case CG_MEASURE_DFMA: k = (const void *)&k_fp64_rate<CG_MEASURE_DFMA>; def = 4096; break;
-    case CG_MEASURE_DADD: k = (const void *)&k_fp64_rate<CG_MEASURE_DADD>; def = 4096; break;
-    case CG_MEASURE_DMUL: k = (const void *)&k_fp64_rate<CG_MEASURE_DMUL>; def = 4096; break;
-    case CG_MEASURE_TANH: k = (const void *)&k_fp64_rate<CG_MEASURE_TANH>; def = 128; break;
-    case CG_MEASURE_EXP: k = (const void *)&k_fp64_rate<CG_MEASURE_EXP>; def = 128; break;
-    case CG_MEASURE_DIV: k = (const void *)&k_fp64_rate<CG_MEASURE_DIV>; def = 256; break;
+    case CG_MEASURE_DFMA: k = (const void *)&k_fp64_rate<CG_MEASURE_DFMA>; def = 40960; break;
+    case CG_MEASURE_DADD: k = (const void *)&k_fp64_rate<CG_MEASURE_DADD>; def = 40960; break;
+    case CG_MEASURE_DMUL: k = (const void *)&k_fp64_rate<CG_MEASURE_DMUL>; def = 40960; break;
+    case CG_MEASURE_TANH: k = (const void *)&k_fp64_rate<CG_MEASURE_TANH>; def = 2048; break;
+    case CG_MEASURE_EXP: k = (const void *)&k_fp64_rate<CG_MEASURE_EXP>; def = 2048; break;
+    case CG_MEASURE_DIV: k = (const void *)&k_fp64_rate<CG_MEASURE_DIV>; def = 4096; break;
     default: return CG_EINVAL;
     }
     if (iters <= 0) iters = def;
@@ -65,7 +65,7 @@ CG_API cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per
     const int grid = sms * 4, block = 256;
     if (e == cudaSuccess) {
         double seed = 0.5;
-        int64_t warm = iters / 8 + 1;
+        int64_t warm = iters / 2 + 1;
         void *wargs[] = {&out, &warm, &seed};
         e = cudaLaunchKernel(k, dim3(grid), dim3(block), wargs, 0, st);
         void *args[] = {&out, &iters, &seed};

@@ -232,15 +232,26 @@ struct Stepper {
         if (want_halo) h = __ldcg(rp + hx);
     }
 
-    // Process stage s of step `step` on local tile lt of instance I.
-    __device__ __forceinline__ static uint32_t tile(const RunArgs &a, const Inst &I, const double *mp, int lt, int s,
-                                    int64_t step, int lane)
+    // Store CX values of one row; `own` has bit c set for every stored cell.
+    __device__ static inline void store_row(double *rp, int x0, bool vec, unsigned own, const double (&v)[CX])
+    {
+        if (CX == 2 && vec && own == 3u) {
+            __stcg(reinterpret_cast<double2 *>(rp + x0), make_double2(v[0], v[CX - 1]));
+        } else {
+#pragma unroll
+            for (int c = 0; c < CX; ++c)
+                if (own & (1u << c)) __stcg(rp + x0 + c, v[c]);
+        }
+    }
+
+    // Stage s of step `step` on columns [xt, xt + 32 CX) x rows y0..y1 of
+    // instance I.  Row mrow_a stores only columns [ma0, ma1), row mrow_b only
+    // [mb0, mb1).
+    __device__ __forceinline__ static uint32_t seg(const RunArgs &a, const Inst &I, const double *mp, int xt,
+                                                   int y0, int y1, int mrow_a, int ma0, int ma1, int mrow_b,
+                                                   int mb0, int mb1, int s, int64_t step, int lane)
     {
         const int nx = I.nx, ny = I.ny, bc = a.bc;
-        const int tx = lt % I.tiles_x, ty = lt / I.tiles_x;
-        const int xt = tx * 32 * CX;
-        const int y0 = ty * a.rows;
-        const int nrows = min(a.rows, ny - y0);
         const int64_t plane = (int64_t)nx * ny;
 
         double *blk = a.ws + I.ws_off;
@@ -265,7 +276,18 @@ struct Stepper {
         for (int c = 0; c < CX; ++c) cx[c] = map_idx(x0 + c, nx, bc);
         const bool want_halo = (lane == 0) || (lane == 31);
         const int hx = map_idx(lane == 0 ? xt - 1 : xt + 32 * CX, nx, bc);
-        const bool full = (x0 + CX - 1) < nx;     // every cell of this lane is stored
+        const bool full = (x0 + CX - 1) < nx;     // every cell of this lane is inside the grid
+        unsigned in_grid = 0;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) in_grid |= (x0 + c < nx) ? (1u << c) : 0u;
+        unsigned own_a = 0, own_b = 0;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            own_a |= (x0 + c >= ma0 && x0 + c < ma1) ? (1u << c) : 0u;
+            own_b |= (x0 + c >= mb0 && x0 + c < mb1) ? (1u << c) : 0u;
+        }
+        own_a &= in_grid;
+        own_b &= in_grid;
         const bool aligned_base = I.vec_ok != 0;
         auto vec_for = [&](const void *p) {
             return CX == 2 && aligned_base && full && ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
@@ -293,12 +315,12 @@ struct Stepper {
         }
 
         uint32_t bad = 0;
-        for (int r = 0; r < nrows; ++r) {
-            const int y = y0 + r;
+        for (int y = y0; y <= y1; ++y) {
             const int yn = map_idx(y + 1, ny, bc);
 #pragma unroll
             for (int f = 0; f < ND; ++f)
                 load_row(Yin + f * plane, nx, yn, cx, hx, vin, want_halo, hi[f], hhi[f]);
+            const unsigned own = (y == mrow_a) ? own_a : ((y == mrow_b) ? own_b : in_grid);
 
             // centre values of every field
             double zc[CX][NV];
@@ -374,19 +396,11 @@ struct Stepper {
                 double outv[CX];
 #pragma unroll
                 for (int c = 0; c < CX; ++c) outv[c] = fma(ca, F[c][f], base[c]);
-                double *op = (last ? dst : acc) + f * plane + ro;
-                const bool vo = last ? vdst : vacc;
-                if (CX == 2 && vo) {
-                    __stcg(reinterpret_cast<double2 *>(op + x0), make_double2(outv[0], outv[CX - 1]));
-                } else {
-#pragma unroll
-                    for (int c = 0; c < CX; ++c)
-                        if (x0 + c < nx) __stcg(op + x0 + c, outv[c]);
-                }
+                store_row((last ? dst : acc) + f * plane + ro, x0, last ? vdst : vacc, own, outv);
                 if (last) {
 #pragma unroll
                     for (int c = 0; c < CX; ++c)
-                        if (x0 + c < nx) bad |= nonfinite_bit(outv[c]);
+                        if (own & (1u << c)) bad |= nonfinite_bit(outv[c]);
                 } else {
                     double zz[CX];
                     if (s == 0) {
@@ -399,14 +413,7 @@ struct Stepper {
                     double yv[CX];
 #pragma unroll
                     for (int c = 0; c < CX; ++c) yv[c] = fma(cyv, F[c][f], zz[c]);
-                    double *yp = Ynext + f * plane + ro;
-                    if (CX == 2 && vyn) {
-                        __stcg(reinterpret_cast<double2 *>(yp + x0), make_double2(yv[0], yv[CX - 1]));
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < CX; ++c)
-                            if (x0 + c < nx) __stcg(yp + x0 + c, yv[c]);
-                    }
+                    store_row(Ynext + f * plane + ro, x0, vyn, own, yv);
                 }
             }
 
@@ -423,6 +430,16 @@ struct Stepper {
             }
         }
         return bad;
+    }
+
+    // Queue tile lt of instance I: rows [ty*rows, ...) x columns of tile tx.
+    __device__ __forceinline__ static uint32_t tile(const RunArgs &a, const Inst &I, const double *mp, int lt,
+                                                    int s, int64_t step, int lane)
+    {
+        const int tx = lt % I.tiles_x, ty = lt / I.tiles_x;
+        const int y0 = ty * a.rows;
+        const int y1 = min(y0 + a.rows, I.ny) - 1;
+        return seg(a, I, mp, tx * 32 * CX, y0, y1, -1, 0, 0, -1, 0, 0, s, step, lane);
     }
 };
 
@@ -444,33 +461,53 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
         }
         return lo;
     };
+    // static schedule: this warp's segments
+    const int gw = blockIdx.x * nwarps + warp;
+    const int sbeg = (a.sched == SCHED_STATIC) ? a.warp_seg[gw] : 0;
+    const int send = (a.sched == SCHED_STATIC) ? a.warp_seg[gw + 1] : 0;
+    auto run_static = [&](int s, int64_t step) {
+        for (int k = sbeg; k < send; ++k) {
+            const Seg sg = a.segs[k];
+            const Inst &I = a.inst[sg.inst];
+            bad |= S::seg(a, I, mp, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b, sg.mb0, sg.mb1,
+                          s, step, lane);
+        }
+    };
 
     if (!a.persistent) {
         const int64_t g = a.g_begin;
         const int s = (int)(g % NS);
         const int64_t step = g / NS;
-        for (int t = blockIdx.x * nwarps + warp; t < a.n_tiles; t += gridDim.x * nwarps) {
-            const int i = find_inst(t);
-            const Inst &I = a.inst[i];
-            bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+        if (a.sched == SCHED_STATIC) {
+            run_static(s, step);
+        } else {
+            for (int t = blockIdx.x * nwarps + warp; t < a.n_tiles; t += gridDim.x * nwarps) {
+                const int i = find_inst(t);
+                const Inst &I = a.inst[i];
+                bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+            }
         }
     } else {
         bool first_barrier = true;
         for (int64_t g = a.g_begin; g < a.g_end; ++g) {
             const int s = (int)(g % NS);
             const int64_t step = g / NS;
-            unsigned *q = a.sync + 2 + (int)(g % 3);
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.sync + 2 + (int)((g + 1) % 3), 0u);
-            int t = 0;
-            if (lane == 0) t = (int)atomicAdd(q, 1u);
-            t = __shfl_sync(CG_FULL, t, 0);
-            while (t < a.n_tiles) {
-                int tn = 0;
-                if (lane == 0) tn = (int)atomicAdd(q, 1u);
-                const int i = find_inst(t);
-                const Inst &I = a.inst[i];
-                bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
-                t = __shfl_sync(CG_FULL, tn, 0);
+            if (a.sched == SCHED_STATIC) {
+                run_static(s, step);
+            } else {
+                unsigned *q = a.sync + 2 + (int)(g % 3);
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.sync + 2 + (int)((g + 1) % 3), 0u);
+                int t = 0;
+                if (lane == 0) t = (int)atomicAdd(q, 1u);
+                t = __shfl_sync(CG_FULL, t, 0);
+                while (t < a.n_tiles) {
+                    int tn = 0;
+                    if (lane == 0) tn = (int)atomicAdd(q, 1u);
+                    const int i = find_inst(t);
+                    const Inst &I = a.inst[i];
+                    bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+                    t = __shfl_sync(CG_FULL, tn, 0);
+                }
             }
             if (g + 1 < a.g_end) {
                 const uint32_t expect = a.nblocks_expect + ((first_barrier && a.stuck_barrier) ? 1u : 0u);

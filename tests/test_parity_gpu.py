@@ -44,8 +44,9 @@ def test_fhn_matrix(cuda_ok, stencil, scheme, bc, shape):
 
 
 @pytest.mark.parametrize("tuning", [
-    dict(cells_x=1, rows=1, threads=128), dict(cells_x=2, rows=3, threads=512),
-    dict(cells_x=1, rows=16, threads=256, blocks_per_sm=1), dict(cells_x=2, rows=64, threads=128),
+    dict(cells_x=1, rows=1, threads=128, schedule=1), dict(cells_x=2, rows=3, threads=512, schedule=1),
+    dict(cells_x=1, rows=16, threads=256, blocks_per_sm=1, schedule=1), dict(cells_x=2, rows=64, threads=128, schedule=1),
+    dict(cells_x=1, threads=256), dict(cells_x=2, threads=128, blocks_per_sm=2), dict(cells_x=1, threads=512),
 ])
 @pytest.mark.parametrize("per_stage", [False, True])
 def test_fhn_tunings_and_launch_modes(cuda_ok, tuning, per_stage):
