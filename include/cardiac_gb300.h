@@ -162,6 +162,51 @@ cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_step
  * CG_ETIMEOUT when the matching bit is set, CG_OK otherwise. */
 cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags);
 
+/* ------------------------------------------------- tangent-linear model */
+
+/* The paper's motivation (Sect. 1) is matrix-free Newton-Krylov solvers that
+ * need the Jacobian of finite-time flows, which it obtains by finite
+ * differences of nearby double-precision solutions.  These calls give the
+ * exact Jacobian-vector products of the discrete flow instead: each RK
+ * stage Y_s of the primal run is differentiated, dk_s = D L dY_s +
+ * dN/dz(Y_s) dY_s, dY_s = dz + dt a_s dk_{s-1}, dz' = dz + dt sum b_s dk_s. */
+
+/* Bytes of workspace cg_tlm_run needs for n_tangents tangents (single-
+ * instance plans only; CG_EUNSUPPORTED for a batch plan). */
+cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t *bytes);
+
+/* Advance the primal state z0 -> zT and n_tangents >= 0 tangents dz0 -> dzT
+ * (device buffers; tangents packed [n_tangents][n_v][ny][nx]) by n_steps
+ * explicit steps: dzT[i] = (d Phi / d z)(z0) dz0[i] with Phi the n-step
+ * discrete flow map.  All tangents share the primal trajectory, advanced
+ * once.  In-place (zT == z0, dzT == dz0) is allowed for Heun and RK4. */
+cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, double *zT, double *dzT,
+                     int32_t n_tangents, int64_t n_steps, void *workspace, void *stream);
+
+/* ------------------------------------------------------ discrete adjoint */
+
+/* Bytes of workspace cg_adjoint_run needs (single-instance plans): the
+ * primal scratch, ceil(n_steps / c) checkpoints, the c*n_stages + 1 stage
+ * inputs of one segment, four adjoint states and one partial sum per warp,
+ * c = checkpoint_every (0 selects ceil(sqrt(n_steps))). */
+cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, size_t *bytes);
+
+/* Reverse-mode derivative of the n-step discrete flow map z0 -> zT (the
+ * transpose of the Jacobian that cg_tlm_run applies).  Given lamT = dL/dzT
+ * (device, [n_v][ny][nx]) it writes lam0 = dL/dz0 (device, may equal lamT)
+ * and, for each diffusive field f, dLdD[f] = dL/dD_f (device, n_diffusive
+ * doubles: 2 for FHN, 1 otherwise), where field f's tensor is
+ * D_f diag(1, Dyy_f/Dxx_f) with the anisotropy ratio held fixed.
+ *
+ * The forward trajectory is rebuilt from checkpoints: one forward sweep
+ * stores z every c steps; then, segment by segment in reverse, the segment
+ * is recomputed keeping every RK stage input and swept back with the
+ * adjoint stage kernel (transposed stencil W L W^-1 under MIRROR ghosts,
+ * transposed local Jacobian).  Cost: two forward runs plus one adjoint run.
+ * dL/dD partial sums are reduced in a fixed order (bitwise reproducible). */
+cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
+                         int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream);
+
 /* ----------------------------------------------------------------- misc */
 
 /* Message describing the last error on the calling thread ("" if none). */

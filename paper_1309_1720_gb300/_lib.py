@@ -55,6 +55,15 @@ _SIGS = {
                               ctypes.c_void_p, ctypes.c_void_p]),
     "cg_read_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_uint32)]),
+    "cg_tlm_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_tlm_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "cg_adjoint_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_adjoint_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_n_fields": (ctypes.c_int32, [ctypes.c_int32]),
     "cg_n_params": (ctypes.c_int32, [ctypes.c_int32]),

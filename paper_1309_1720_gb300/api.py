@@ -181,6 +181,47 @@ class Plan:
                                 _stream_handle(stream)))
         return out
 
+    def tlm_workspace(self, n_tangents: int) -> torch.Tensor:
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_tlm_workspace_size(self._h, int(n_tangents), ctypes.byref(sz)))
+        if self._ws is None or self._ws.numel() < sz.value:
+            self._ws = torch.empty(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def tlm(self, z0: torch.Tensor, dz0: torch.Tensor, n_steps: int, zT: Optional[torch.Tensor] = None,
+            dzT: Optional[torch.Tensor] = None, stream=None):
+        """Exact Jacobian-vector products of the n-step flow map: returns
+        (zT, dzT) with dzT[i] = dPhi/dz(z0) dz0[i]; dz0 is [T, n_v, ny, nx]."""
+        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        assert dz0.is_cuda and dz0.dtype == torch.float64 and dz0.is_contiguous()
+        n_t = dz0.numel() // z0.numel()
+        assert n_t * z0.numel() == dz0.numel()
+        zT = torch.empty_like(z0) if zT is None else zT
+        dzT = torch.empty_like(dz0) if dzT is None else dzT
+        ws = self.tlm_workspace(n_t)
+        check(_lib.lib().cg_tlm_run(self._h, z0.data_ptr(), dz0.data_ptr(), zT.data_ptr(), dzT.data_ptr(),
+                                    n_t, int(n_steps), ws.data_ptr(), _stream_handle(stream)))
+        return zT, dzT
+
+    def adjoint(self, z0: torch.Tensor, lamT: torch.Tensor, n_steps: int, checkpoint_every: int = 0,
+                stream=None):
+        """Reverse-mode derivative of the n-step flow map: returns
+        (lam0, dLdD) with lam0 = dL/dz0 for lamT = dL/dzT and dLdD the
+        derivatives w.r.t. each diffusive field's D (device tensors)."""
+        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        assert lamT.is_cuda and lamT.dtype == torch.float64 and lamT.is_contiguous()
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_adjoint_workspace_size(self._h, int(n_steps), int(checkpoint_every), ctypes.byref(sz)))
+        if self._ws is None or self._ws.numel() < sz.value:
+            self._ws = torch.empty(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+        lam0 = torch.empty_like(lamT)
+        nd = 2 if self.model == FHN else 1
+        dLdD = torch.empty(nd, dtype=torch.float64, device="cuda")
+        check(_lib.lib().cg_adjoint_run(self._h, z0.data_ptr(), lamT.data_ptr(), lam0.data_ptr(), dLdD.data_ptr(),
+                                        int(n_steps), int(checkpoint_every), self._ws.data_ptr(),
+                                        _stream_handle(stream)))
+        return lam0, dLdD
+
     def status(self, stream=None, workspace: Optional[torch.Tensor] = None, raise_on_error: bool = True) -> int:
         ws = self.workspace() if workspace is None else workspace
         flags = ctypes.c_uint32()

@@ -12,6 +12,8 @@
 #include <vector>
 
 #include "cg_internal.h"
+#include "cg_tlm.cuh"
+#include "cg_adjoint.cuh"
 
 #define CG_API extern "C" __attribute__((visibility("default")))
 
@@ -118,6 +120,7 @@ struct cg_plan_s {
     uint64_t timeout_ns = 0;
     const void *kernel = nullptr;
     int nblocks = 0;
+    double dxx[4] = {};              // Dxx of the first instance (gradient normalisation)
 };
 
 namespace {
@@ -241,6 +244,14 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         P.mp[38] = 1.0 / prm[8];        // 1/tvp
         P.mp[39] = 1.0 / prm[13];       // 1/twp
         P.mp[40] = 1.0 / prm[26];       // 1/twinf
+        P.mp[41] = -prm[11] * prm[12];  // -kwm uwm
+        P.mp[42] = -prm[19] * prm[20];  // -kso uso
+        P.mp[43] = -prm[23] * prm[24];  // -ks us
+        P.mp[44] = (prm[10] - prm[9]) / 2.0;    // (tw2m - tw1m) / 2
+        P.mp[45] = (prm[9] + prm[10]) / 2.0;    // (tw1m + tw2m) / 2
+        P.mp[46] = (prm[18] - prm[17]) / 2.0;   // (tso2 - tso1) / 2
+        P.mp[47] = (prm[17] + prm[18]) / 2.0;   // (tso1 + tso2) / 2
+        P.mp[48] = 6.0 * k;                     // 6 k
         I.mi[0] = I.wc[0];
     }
 }
@@ -355,6 +366,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     P->ns = n_stages(p0.scheme);
     P->flags = p0.flags;
     P->dt = p0.dt;
+    for (int f = 0; f < 4; ++f) P->dxx[f] = p0.Dxx[f];
     const double tmo = p0.barrier_timeout_s > 0 ? p0.barrier_timeout_s : 10.0;
     P->timeout_ns = (uint64_t)(std::min(tmo, 3600.0) * 1e9);
 
@@ -480,6 +492,60 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     return CG_OK;
 }
 
+// Run global stages [g0, g1) of a kernel whose first argument is `a`: one
+// cooperative persistent launch (grid barriers between stages), or with
+// CG_FLAG_PER_STAGE_LAUNCH one ordinary launch of `stage_grid` blocks per
+// stage.
+cg_status launch_stages(cg_plan P, const void *kernel, void **args, RunArgs &a, int64_t g0, int64_t g1,
+                        int stage_grid, cudaStream_t s)
+{
+    cudaError_t e;
+    if (g1 <= g0) return CG_OK;
+    if (P->flags & CG_FLAG_PER_STAGE_LAUNCH) {
+        a.persistent = 0;
+        for (int64_t g = g0; g < g1; ++g) {
+            a.g_begin = g;
+            a.g_end = g + 1;
+            e = cudaLaunchKernel(kernel, dim3(stage_grid), dim3(P->threads), args, 0, s);
+            if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+        }
+        return CG_OK;
+    }
+    a.persistent = 1;
+    a.g_begin = g0;
+    a.g_end = g1;
+    a.nblocks_expect = (uint32_t)P->nblocks;
+    a.stuck_barrier = (P->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(P->nblocks);
+    cfg.blockDim = dim3(P->threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, kernel, args);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+    return CG_OK;
+}
+
+// Co-residency of a secondary kernel (tangent / adjoint) on the plan's grid.
+cg_status check_coresident(cg_plan P, const void *kernel)
+{
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, P->threads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ * P->num_sms < P->nblocks)
+        return fail(CG_EUNSUPPORTED, "kernel fits %d blocks per SM; the plan's grid needs %d", occ,
+                    (P->nblocks + P->num_sms - 1) / P->num_sms);
+    return CG_OK;
+}
+
+int64_t round32(int64_t n) { return (n + 31) / 32 * 32; }
+
 cg_status check_plan_device(cg_plan P)
 {
     int dev = -1;
@@ -592,36 +658,10 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     const int64_t G = n_steps * plan->ns;
     void *args[] = {&a};
 
-    if (plan->flags & CG_FLAG_PER_STAGE_LAUNCH) {
-        const int wpb = plan->threads / 32;
-        const int grid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
-        a.persistent = 0;
-        for (int64_t g = 0; g < G; ++g) {
-            a.g_begin = g;
-            a.g_end = g + 1;
-            e = cudaLaunchKernel(plan->kernel, dim3(grid), dim3(plan->threads), args, 0, s);
-            if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
-        }
-    } else {
-        a.persistent = 1;
-        a.g_begin = 0;
-        a.g_end = G;
-        a.nblocks_expect = (uint32_t)plan->nblocks;
-        a.stuck_barrier = (plan->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof cfg);
-        cfg.gridDim = dim3(plan->nblocks);
-        cfg.blockDim = dim3(plan->threads);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, plan->kernel, args);
-        if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
-    }
+    const int wpb = plan->threads / 32;
+    const int qgrid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
+    st = launch_stages(plan, plan->kernel, args, a, 0, G, qgrid, s);
+    if (st != CG_OK) return st;
     if (alias_single_stage && (n_steps & 1)) {
         // odd number of single-stage steps in place: the last result sits in
         // the scratch copy of each instance
@@ -649,6 +689,263 @@ CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *strea
     if (v & CG_DEV_TIMEOUT) return fail(CG_ETIMEOUT, "a device-side wait gave up (status 0x%x)", v);
     if (v & CG_DEV_NONFINITE) return fail(CG_ENAN, "a non-finite value was written (status 0x%x)", v);
     return CG_OK;
+}
+
+// ----------------------------------------------------------- tangent-linear
+
+namespace {
+
+const void *lookup_tlm_kernel(int model, int stencil, int scheme, int cx)
+{
+    switch (model) {
+    case CG_FHN: return cgk::tlm_kernel_fhn(stencil, scheme, cx);
+    case CG_BOCF: return cgk::tlm_kernel_bocf(stencil, scheme, cx);
+    case CG_DIFFUSION: return cgk::tlm_kernel_diff(stencil, scheme, cx);
+    default: return nullptr;
+    }
+}
+
+// Workspace of cg_tlm_run: header | primal scratch | J planes | tangent scratch.
+struct TlmLayout {
+    size_t jbuf_off, tan_off, total;
+    int64_t tstride, tblk;
+};
+
+TlmLayout tlm_layout(cg_plan P, int32_t n_tan)
+{
+    const Inst &I = P->inst[0];
+    const int64_t plane = (int64_t)I.nx * I.ny;
+    TlmLayout L;
+    L.tstride = (int64_t)P->nv * plane;
+    L.tblk = round32((int64_t)cgk::SCRATCH_PLANES * P->nv * plane);
+    L.jbuf_off = cgk::WS_HEADER + (size_t)P->scratch_elems * sizeof(double);
+    L.tan_off = L.jbuf_off + (size_t)round32(std::max(1, cgk::model_nj(P->model)) * plane) * sizeof(double);
+    L.total = L.tan_off + (size_t)n_tan * (size_t)L.tblk * sizeof(double);
+    return L;
+}
+
+bool overlaps(const void *a, const void *b, size_t n)
+{
+    const char *x = reinterpret_cast<const char *>(a), *y = reinterpret_cast<const char *>(b);
+    return x != y && x < y + n && y < x + n;
+}
+
+// Fill the fields of RunArgs shared by every single-instance launch.
+void base_args(cg_plan P, RunArgs &a, const double *z_in, double *z_out, char *ws)
+{
+    std::memset(&a, 0, sizeof a);
+    a.inst = P->d_inst;
+    a.segs = P->d_segs;
+    a.warp_seg = P->d_warp_seg;
+    a.sched = cgk::SCHED_STATIC;
+    a.n_inst = (int32_t)P->inst.size();
+    a.n_tiles = P->n_tiles;
+    a.bc = P->bc;
+    a.rows = P->rows;
+    a.z_in = z_in;
+    a.z_out = z_out;
+    a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
+    a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
+    a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
+    a.timeout_ns = P->timeout_ns;
+    std::memcpy(a.cacc, P->cacc, sizeof a.cacc);
+    std::memcpy(a.cy, P->cy, sizeof a.cy);
+    std::memcpy(a.mp, P->mp, sizeof a.mp);
+}
+
+}  // namespace
+
+CG_API cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t *bytes)
+{
+    if (!plan || !bytes || n_tangents < 0) return fail(CG_EINVAL, "bad argument");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    *bytes = tlm_layout(plan, n_tangents).total;
+    return CG_OK;
+}
+
+CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, double *zT, double *dzT,
+                            int32_t n_tangents, int64_t n_steps, void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    if (!z0 || !zT || !workspace || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (n_tangents > 0 && (!dz0 || !dzT)) return fail(CG_EINVAL, "NULL tangent buffer");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    const TlmLayout L = tlm_layout(plan, n_tangents);
+    const size_t sbytes = (size_t)L.tstride * sizeof(double);
+    const size_t tbytes = sbytes * (size_t)n_tangents;
+    if (overlaps(z0, zT, sbytes) || (n_tangents && overlaps(dz0, dzT, tbytes)))
+        return fail(CG_EINVAL, "input and output partially overlap");
+    if (plan->ns == 1 && n_steps > 0 && (z0 == zT || (n_tangents && dz0 == dzT)))
+        return fail(CG_EINVAL, "in-place tangent-linear runs need a multi-stage scheme");
+    cg_status st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    if (n_steps == 0) {
+        if (z0 != zT) e = cudaMemcpyAsync(zT, z0, sbytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && n_tangents && dz0 != dzT)
+            e = cudaMemcpyAsync(dzT, dz0, tbytes, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    const void *k = lookup_tlm_kernel(plan->model, plan->stencil, plan->scheme, plan->cx);
+    if (!k) return fail(CG_EUNSUPPORTED, "no tangent-linear kernel for this problem");
+    st = check_coresident(plan, k);
+    if (st != CG_OK) return st;
+    RunArgs a;
+    base_args(plan, a, z0, zT, ws);
+    a.parity = (int32_t)((n_steps - 1) & 1);
+    cgk::TlmArgs t;
+    std::memset(&t, 0, sizeof t);
+    t.dz_in = dz0;
+    t.dz_out = dzT;
+    t.jbuf = reinterpret_cast<double *>(ws + L.jbuf_off);
+    t.tws = reinterpret_cast<double *>(ws + L.tan_off);
+    t.n_tan = n_tangents;
+    t.tstride = L.tstride;
+    t.tblk = L.tblk;
+    void *args[] = {&a, &t};
+    return launch_stages(plan, k, args, a, 0, n_steps * plan->ns, plan->nblocks, s);
+}
+
+// ------------------------------------------------------------------ adjoint
+
+namespace {
+
+const void *lookup_adj_kernel(int model, int stencil, int scheme, int cx)
+{
+    switch (model) {
+    case CG_FHN: return cgk::adj_kernel_fhn(stencil, scheme, cx);
+    case CG_BOCF: return cgk::adj_kernel_bocf(stencil, scheme, cx);
+    case CG_DIFFUSION: return cgk::adj_kernel_diff(stencil, scheme, cx);
+    default: return nullptr;
+    }
+}
+
+// Workspace of cg_adjoint_run: header | primal scratch | checkpoints |
+// segment store | kb0 kb1 lam lacc | per-warp dL/dD partials.
+struct AdjLayout {
+    int64_t c, nseg, S;
+    size_t cp_off, store_off, kb_off, part_off, total;
+};
+
+AdjLayout adj_layout(cg_plan P, int64_t n_steps, int32_t every)
+{
+    AdjLayout L;
+    const Inst &I = P->inst[0];
+    L.S = round32((int64_t)P->nv * I.nx * I.ny);
+    L.c = every > 0 ? every : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(1, n_steps))));
+    L.nseg = std::max<int64_t>(1, (n_steps + L.c - 1) / L.c);
+    const size_t d = sizeof(double);
+    L.cp_off = cgk::WS_HEADER + (size_t)P->scratch_elems * d;
+    L.store_off = L.cp_off + (size_t)L.nseg * L.S * d;
+    L.kb_off = L.store_off + (size_t)(L.c * P->ns + 1) * L.S * d;
+    L.part_off = L.kb_off + (size_t)4 * L.S * d;
+    const int nd = P->model == CG_FHN ? 2 : 1;
+    L.total = L.part_off + (size_t)round32((int64_t)P->nblocks * (P->threads / 32) * nd) * d;
+    return L;
+}
+
+}  // namespace
+
+CG_API cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, size_t *bytes)
+{
+    if (!plan || !bytes || n_steps < 0 || checkpoint_every < 0) return fail(CG_EINVAL, "bad argument");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
+    *bytes = adj_layout(plan, n_steps, checkpoint_every).total;
+    return CG_OK;
+}
+
+CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
+                                int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
+    if (!z0 || !lamT || !lam0 || !dLdD || !workspace || n_steps < 0 || checkpoint_every < 0)
+        return fail(CG_EINVAL, "bad argument");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    cg_status st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    const AdjLayout L = adj_layout(plan, n_steps, checkpoint_every);
+    const Inst &I = plan->inst[0];
+    const int64_t nstate = (int64_t)plan->nv * I.nx * I.ny;
+    const size_t sbytes = (size_t)nstate * sizeof(double);
+    if (overlaps(lamT, lam0, sbytes)) return fail(CG_EINVAL, "lamT and lam0 partially overlap");
+    const int nd = plan->model == CG_FHN ? 2 : 1;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    double *cp = reinterpret_cast<double *>(ws + L.cp_off);
+    double *store = reinterpret_cast<double *>(ws + L.store_off);
+    double *kb = reinterpret_cast<double *>(ws + L.kb_off);
+    double *part = reinterpret_cast<double *>(ws + L.part_off);
+    const int nwarps = plan->nblocks * (plan->threads / 32);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nwarps * nd, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (n_steps == 0) {
+        if (lam0 != lamT) e = cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    const void *ka = lookup_adj_kernel(plan->model, plan->stencil, plan->scheme, plan->cx);
+    if (!ka) return fail(CG_EUNSUPPORTED, "no adjoint kernel for this problem");
+    st = check_coresident(plan, ka);
+    if (st != CG_OK) return st;
+
+    // 1. forward sweep keeping a checkpoint every c steps
+    e = cudaMemcpyAsync(cp, z0, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(checkpoint)");
+    RunArgs a;
+    for (int64_t j = 1; j < L.nseg; ++j) {
+        base_args(plan, a, cp + (j - 1) * L.S, cp + j * L.S, ws);
+        a.parity = (int32_t)((L.c - 1) & 1);
+        void *args[] = {&a};
+        st = launch_stages(plan, plan->kernel, args, a, 0, L.c * plan->ns, plan->nblocks, s);
+        if (st != CG_OK) return st;
+    }
+    // 2. lam = lamT, kb = dt b_last lamT
+    double *lam = kb + 2 * L.S, *lacc = kb + 3 * L.S;
+    e = cudaMemcpyAsync(lam, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam)");
+    cgk::k_scale<<<plan->num_sms * 4, 256, 0, s>>>(kb, lamT, plan->cacc[plan->ns - 1], nstate);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "scale kernel");
+    // 3. segments in reverse: recompute with every stage kept, then sweep back
+    int64_t r = 0;
+    for (int64_t j = L.nseg - 1; j >= 0; --j) {
+        const int64_t m = std::min<int64_t>(L.c, n_steps - j * L.c);
+        base_args(plan, a, cp + j * L.S, store + m * plan->ns * L.S, ws);
+        a.store = store;
+        void *fargs[] = {&a};
+        st = launch_stages(plan, plan->kernel, fargs, a, 0, m * plan->ns, plan->nblocks, s);
+        if (st != CG_OK) return st;
+        base_args(plan, a, cp + j * L.S, nullptr, ws);
+        cgk::AdjArgs b;
+        b.store = store;
+        b.kb0 = kb;
+        b.kb1 = kb + L.S;
+        b.lam = lam;
+        b.lacc = lacc;
+        b.partial = part;
+        b.m = m;
+        b.r0 = r;
+        void *aargs[] = {&a, &b};
+        st = launch_stages(plan, ka, aargs, a, 0, m * plan->ns, plan->nblocks, s);
+        if (st != CG_OK) return st;
+        r += m * plan->ns;
+    }
+    // 4. outputs
+    e = cudaMemcpyAsync(lam0, lam, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam0)");
+    cgk::Inv4 inv;
+    for (int f = 0; f < 4; ++f) inv.v[f] = plan->dxx[f] != 0.0 ? 1.0 / plan->dxx[f] : 0.0;
+    cgk::k_reduce_partials<<<1, 32, 0, s>>>(part, nwarps, nd, inv, dLdD);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "reduce kernel");
 }
 
 CG_API const char *cg_last_error(void)

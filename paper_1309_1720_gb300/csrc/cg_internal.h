@@ -10,7 +10,7 @@
 namespace cgk {
 
 constexpr int MAXF = 4;     // fields per cell (BOCF: u, v, w, s)
-constexpr int NMP = 48;     // model constants shared by all instances of a plan
+constexpr int NMP = 56;     // model constants shared by all instances of a plan
 
 // One grid instance, resident in a plan-owned device table.  Coefficients
 // carry D/dx^2 and the stencil weights; the centre weight is folded into the
@@ -49,6 +49,7 @@ struct RunArgs {
     const double *z_in;
     double *z_out;
     double *ws;                  // base of the per-instance scratch blocks
+    double *store;               // optional: keep every stage input (single instance; see Bufs)
     unsigned *sync;              // [0] barrier count, [1] barrier generation, [2..4] tile queues
     uint32_t *status;            // device status word (CG_DEV_*)
     int64_t g_begin, g_end;      // global stage range [g_begin, g_end) of this launch
@@ -77,5 +78,17 @@ enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION };
 const void *fwd_kernel_fhn(int stencil, int scheme, int cx);
 const void *fwd_kernel_bocf(int stencil, int scheme, int cx);
 const void *fwd_kernel_diff(int stencil, int scheme, int cx);
+const void *tlm_kernel_fhn(int stencil, int scheme, int cx);
+const void *tlm_kernel_bocf(int stencil, int scheme, int cx);
+const void *tlm_kernel_diff(int stencil, int scheme, int cx);
+const void *adj_kernel_fhn(int stencil, int scheme, int cx);
+const void *adj_kernel_bocf(int stencil, int scheme, int cx);
+const void *adj_kernel_diff(int stencil, int scheme, int cx);
+
+// Stored Jacobian entries per cell of each model (0 for the linear model).
+inline int model_nj(int model)
+{
+    return model == CG_FHN ? 1 : model == CG_BOCF ? 10 : 0;
+}
 
 }  // namespace cgk

@@ -115,6 +115,9 @@ template <int M> struct Model;
 //   F_v = eps u + (wc_v - eps a1) v - eps a0 + stencil_v
 template <> struct Model<MODEL_FHN> {
     static constexpr int NV = 2, ND = 2;
+    // Jacobian entries stored per cell: J0 = d t_u / d u = (1 + wc_u) - 3 u^2
+    // (the other entries, -1, eps and wc_v - eps a1, are constants).
+    static constexpr int NJ = 1;
     struct Coef { double A_u, B_v; };
     __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.mi[1]}; }
     // mp[0] = eps, mp[1] = -eps a0 ; Coef holds instance-dependent folds.
@@ -125,16 +128,54 @@ template <> struct Model<MODEL_FHN> {
         t[0] = fma(-p, u, fma(c.A_u, u, -v));
         t[1] = fma(mp[0], u, fma(c.B_v, v, mp[1]));
     }
+    __device__ static void local_jac(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV],
+                                     double (&J)[NJ])
+    {
+        const double u = z[0], v = z[1];
+        const double p = u * u;
+        t[0] = fma(-p, u, fma(c.A_u, u, -v));
+        t[1] = fma(mp[0], u, fma(c.B_v, v, mp[1]));
+        J[0] = fma(-3.0, p, c.A_u);
+    }
+    // tangent: J d with the centre weights folded in
+    __device__ static void tan_local(const Coef &c, const double *mp, const double (&J)[NJ],
+                                     const double (&d)[NV], double (&t)[NV])
+    {
+        t[0] = fma(J[0], d[0], -d[1]);
+        t[1] = fma(mp[0], d[0], c.B_v * d[1]);
+    }
+    // adjoint: J^T k with the centre weights folded in
+    __device__ static void adj_local(const Coef &c, const double *mp, const double (&J)[NJ],
+                                     const double (&k)[NV], double (&t)[NV])
+    {
+        t[0] = fma(J[0], k[0], mp[0] * k[1]);
+        t[1] = fma(c.B_v, k[1], -k[0]);
+    }
 };
 
 // Pure diffusion (N = 0), one field: F = wc u + stencil.
 template <> struct Model<MODEL_DIFF> {
-    static constexpr int NV = 1, ND = 1;
+    static constexpr int NV = 1, ND = 1, NJ = 0;
     struct Coef { double wc; };
     __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0]}; }
     __device__ static void local(const Coef &c, const double *, const double (&z)[NV], double (&t)[NV])
     {
         t[0] = c.wc * z[0];
+    }
+    __device__ static void local_jac(const Coef &c, const double *, const double (&z)[NV], double (&t)[NV],
+                                     double (&)[1])
+    {
+        t[0] = c.wc * z[0];
+    }
+    __device__ static void tan_local(const Coef &c, const double *, const double (&)[1], const double (&d)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = c.wc * d[0];
+    }
+    __device__ static void adj_local(const Coef &c, const double *, const double (&)[1], const double (&k)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = c.wc * k[0];
     }
 };
 
@@ -161,38 +202,121 @@ enum {
     BD_IVP,            // 1/tvp
     BD_IWP,            // 1/twp
     BD_IWINF,          // 1/twinf
+    BD_AWM,            // -kwm uwm
+    BD_ASO,            // -kso uso
+    BD_AS,             // -ks us
+    BD_HDTW,           // (tw2m - tw1m) / 2
+    BD_MTW,            // (tw1m + tw2m) / 2
+    BD_HDSO,           // (tso2 - tso1) / 2
+    BD_MSO,            // (tso1 + tso2) / 2
+    BD_6K,             // 6 k
     BD_N
 };
 
 template <> struct Model<MODEL_BOCF> {
     static constexpr int NV = 4, ND = 1;
+    // Stored Jacobian entries (wc_u folded into J_uu):
+    // [J_uu, J_uv, J_uw, J_us, J_vu, J_vv, J_wu, J_ww, J_su, J_ss]
+    static constexpr int NJ = 10;
     struct Coef { double wc_u; };
     __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0]}; }
-    __device__ static void local(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV])
+
+    // Shared body: right-hand side t and, when JAC, the Jacobian entries.
+    // Sigmoids (1 + tanh(a))/2 are written with tanh; time constants enter
+    // through their reciprocals.
+    template <bool JAC>
+    __device__ __forceinline__ static void eval(const Coef &c, const double *mp, const double (&z)[NV],
+                                                double (&t)[NV], double *J)
     {
         const double u = z[0], v = z[1], w = z[2], s = z[3];
         const double k = mp[BP_K];
-        const double Hv = smooth_step(u, k, mp[BD_CV]);
-        const double Hw = smooth_step(u, k, mp[BD_CW]);
-        const double Hvm = smooth_step(u, k, mp[BD_CVM]);
-        const double Ho = smooth_step(u, k, mp[BD_CO]);
+        const double tv = clamp01_int(fma(k, u, mp[BD_CV]));
+        const double tw = clamp01_int(fma(k, u, mp[BD_CW]));
+        const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
+        const double to = clamp01_int(fma(k, u, mp[BD_CO]));
+        const double Hv = (tv * tv) * fma(-2.0, tv, 3.0);
+        const double Hw = (tw * tw) * fma(-2.0, tw, 3.0);
+        const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);
+        const double Ho = (to * to) * fma(-2.0, to, 3.0);
         const double tau_vm = fma(Hvm, mp[BD_DTV], mp[BP_TV1M]);
+        const double r_vm = 1.0 / tau_vm;
         const double v_inf = 1.0 - Hvm;
-        const double tau_wm = mp[BP_TW1M] + (mp[BP_TW2M] - mp[BP_TW1M]) *
-                              (1.0 + tanh(mp[BP_KWM] * (u - mp[BP_UWM]))) * 0.5;
+        const double th_w = tanh(fma(mp[BP_KWM], u, mp[BD_AWM]));
+        const double r_wm = 1.0 / fma(mp[BD_HDTW], th_w, mp[BD_MTW]);
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
-        const double tau_o = fma(Ho, mp[BD_DTO], mp[BP_TO1]);
-        const double tau_so = mp[BP_TSO1] + (mp[BP_TSO2] - mp[BP_TSO1]) *
-                              (1.0 + tanh(mp[BP_KSO] * (u - mp[BP_USO]))) * 0.5;
-        const double tau_s = fma(Hw, mp[BD_DTS], mp[BP_TS1]);
-        const double J_fi = -v * Hv * (u - mp[BP_THV]) * (mp[BP_UU] - u) * mp[BD_IFI];
-        const double J_so = (u - mp[BP_UO]) * (1.0 - Hw) / tau_o + Hw / tau_so;
-        const double J_si = -Hw * w * s * mp[BD_ISI];
+        const double r_o = 1.0 / fma(Ho, mp[BD_DTO], mp[BP_TO1]);
+        const double th_so = tanh(fma(mp[BP_KSO], u, mp[BD_ASO]));
+        const double r_so = 1.0 / fma(mp[BD_HDSO], th_so, mp[BD_MSO]);
+        const double r_s = 1.0 / fma(Hw, mp[BD_DTS], mp[BP_TS1]);
+        const double th_s = tanh(fma(mp[BP_KS], u, mp[BD_AS]));
+        const double s_inf = fma(0.5, th_s, 0.5);
+        const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
+        const double omHv = 1.0 - Hv, omHw = 1.0 - Hw;
+        const double vinf_v = v_inf - v, winf_w = w_inf - w, sinf_s = s_inf - s;
+        const double J_fi = -(v * Hv) * (ua * ub) * mp[BD_IFI];
+        const double J_so = fma(uo * omHw, r_o, Hw * r_so);
+        const double J_si = -(Hw * w) * (s * mp[BD_ISI]);
         t[0] = fma(c.wc_u, u, -(J_fi + J_so + J_si));
-        t[1] = (1.0 - Hv) * (v_inf - v) / tau_vm - Hv * v * mp[BD_IVP];
-        t[2] = (1.0 - Hw) * (w_inf - w) / tau_wm - Hw * w * mp[BD_IWP];
-        t[3] = ((1.0 + tanh(mp[BP_KS] * (u - mp[BP_US]))) * 0.5 - s) / tau_s;
+        t[1] = fma(omHv * vinf_v, r_vm, -(Hv * v) * mp[BD_IVP]);
+        t[2] = fma(omHw * winf_w, r_wm, -(Hw * w) * mp[BD_IWP]);
+        t[3] = sinf_s * r_s;
+        if constexpr (JAC) {
+            const double k6 = mp[BD_6K];
+            const double dHv = k6 * (tv * (1.0 - tv));
+            const double dHw = k6 * (tw * (1.0 - tw));
+            const double dHvm = k6 * (tvm * (1.0 - tvm));
+            const double dHo = k6 * (to * (1.0 - to));
+            const double dtau_vm = dHvm * mp[BD_DTV];
+            const double dtau_wm = mp[BD_HDTW] * mp[BP_KWM] * fma(-th_w, th_w, 1.0);
+            const double dtau_o = dHo * mp[BD_DTO];
+            const double dtau_so = mp[BD_HDSO] * mp[BP_KSO] * fma(-th_so, th_so, 1.0);
+            const double dtau_s = dHw * mp[BD_DTS];
+            const double dw_inf = fma(dHo, mp[BP_WINFSTAR] - q, -(1.0 - Ho) * mp[BD_IWINF]);
+            const double ds_inf = 0.5 * mp[BP_KS] * fma(-th_s, th_s, 1.0);
+            const double dJfi_du = -(v * mp[BD_IFI]) * fma(dHv, ua * ub, Hv * (ub - ua));
+            const double dJfi_dv = -Hv * (ua * ub) * mp[BD_IFI];
+            const double dJso_du = omHw * r_o - uo * dHw * r_o - uo * omHw * dtau_o * (r_o * r_o)
+                                   + dHw * r_so - Hw * dtau_so * (r_so * r_so);
+            const double dJsi_du = -dHw * (w * s) * mp[BD_ISI];
+            J[0] = c.wc_u - (dJfi_du + dJso_du + dJsi_du);
+            J[1] = -dJfi_dv;
+            J[2] = Hw * s * mp[BD_ISI];
+            J[3] = Hw * w * mp[BD_ISI];
+            J[4] = -dHv * vinf_v * r_vm + omHv * (-dHvm * r_vm - vinf_v * dtau_vm * (r_vm * r_vm))
+                   - dHv * v * mp[BD_IVP];
+            J[5] = -omHv * r_vm - Hv * mp[BD_IVP];
+            J[6] = -dHw * winf_w * r_wm + omHw * (dw_inf * r_wm - winf_w * dtau_wm * (r_wm * r_wm))
+                   - dHw * w * mp[BD_IWP];
+            J[7] = -omHw * r_wm - Hw * mp[BD_IWP];
+            J[8] = ds_inf * r_s - sinf_s * dtau_s * (r_s * r_s);
+            J[9] = -r_s;
+        }
+    }
+    __device__ static void local(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV])
+    {
+        eval<false>(c, mp, z, t, nullptr);
+    }
+    __device__ static void local_jac(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV],
+                                     double (&J)[NJ])
+    {
+        eval<true>(c, mp, z, t, J);
+    }
+    __device__ static void tan_local(const Coef &, const double *, const double (&J)[NJ], const double (&d)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = fma(J[0], d[0], fma(J[1], d[1], fma(J[2], d[2], J[3] * d[3])));
+        t[1] = fma(J[4], d[0], J[5] * d[1]);
+        t[2] = fma(J[6], d[0], J[7] * d[2]);
+        t[3] = fma(J[8], d[0], J[9] * d[3]);
+    }
+    __device__ static void adj_local(const Coef &, const double *, const double (&J)[NJ], const double (&k)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = fma(J[0], k[0], fma(J[4], k[1], fma(J[6], k[2], J[8] * k[3])));
+        t[1] = fma(J[1], k[0], J[5] * k[1]);
+        t[2] = fma(J[2], k[0], J[7] * k[2]);
+        t[3] = fma(J[3], k[0], J[9] * k[3]);
     }
 };
 
@@ -210,12 +334,73 @@ __device__ __forceinline__ int map_idx(int i, int n, int bc)
     return i < n ? i : n - 1;
 }
 
+// ------------------------------------------------------- stencil helpers
+
+// F[c] += wd (V(x-1) + V(x+1)) + wy V(x) + wx (W + E) for the CX cells of a
+// lane, V = N + S (the vertical pair sum), from a three-row window (lo, mid,
+// hi) and the halo column held by lanes 0 (west) and 31 (east).  V(x) is
+// formed once per column and shared with the neighbouring columns, so the
+// 9-point stencil costs three additions and three FMAs per cell.
+template <int ST, int CX>
+__device__ __forceinline__ void add_offcentre(int lane, const double (&lo)[CX], const double (&mid)[CX],
+                                              const double (&hi)[CX], double hlo, double hmid, double hhi,
+                                              double wx, double wy, double wd, double (&F)[CX])
+{
+    double up = __shfl_up_sync(CG_FULL, mid[CX - 1], 1);
+    double dn = __shfl_down_sync(CG_FULL, mid[0], 1);
+    if (lane == 0) up = hmid;
+    if (lane == 31) dn = hmid;
+    double V[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) V[c] = lo[c] + hi[c];
+    double Vl = 0.0, Vr = 0.0;
+    if (ST == CG_STENCIL9) {
+        const double Vh = hlo + hhi;
+        Vl = __shfl_up_sync(CG_FULL, V[CX - 1], 1);
+        Vr = __shfl_down_sync(CG_FULL, V[0], 1);
+        if (lane == 0) Vl = Vh;
+        if (lane == 31) Vr = Vh;
+    }
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+        const double W = (c == 0) ? up : mid[c - 1];
+        const double E = (c == CX - 1) ? dn : mid[c + 1];
+        double acc_f = F[c];
+        if (ST == CG_STENCIL9) {
+            const double VW = (c == 0) ? Vl : V[c - 1];
+            const double VE = (c == CX - 1) ? Vr : V[c + 1];
+            acc_f = fma(wd, VW + VE, acc_f);
+        }
+        acc_f = fma(wy, V[c], acc_f);
+        acc_f = fma(wx, W + E, acc_f);
+        F[c] = acc_f;
+    }
+}
+
 // ------------------------------------------------------------ tile worker
 
-template <int M, int ST, int NS, int CX>
+// Buffers of one state being advanced: input, output, and its scratch block
+// (zb | acc | Ya | Yb).
+// With `store` set, every stage input of every step is kept instead: step k
+// reads its state from store[k*NS] and its stage inputs from store[k*NS + s]
+// and writes store[(k+1)*NS] (states of NV planes each), so that the
+// adjoint sweep can revisit them.
+struct Bufs {
+    const double *zin;
+    double *zout;
+    double *blk;
+    double *store = nullptr;
+};
+
+// What a sweep computes: the model's right-hand side (PRIMAL), the same plus
+// the local Jacobian dN/dz written to jbuf (PRIMAL_J), or the tangent-linear
+// right-hand side D L dz + J dz with J read from jbuf (TANGENT).
+enum { KIND_PRIMAL = 0, KIND_PRIMAL_J = 1, KIND_TANGENT = 2 };
+
+template <int M, int ST, int NS, int CX, int KIND = KIND_PRIMAL>
 struct Stepper {
     using MD = Model<M>;
-    static constexpr int NV = MD::NV, ND = MD::ND;
+    static constexpr int NV = MD::NV, ND = MD::ND, NJ = MD::NJ;
 
     __device__ static inline void load_row(const double *plane, int nx, int yrow, const int (&cx)[CX],
                                            int hx, bool vec, bool want_halo, double (&v)[CX], double &h)
@@ -247,24 +432,32 @@ struct Stepper {
     // Stage s of step `step` on columns [xt, xt + 32 CX) x rows y0..y1 of
     // instance I.  Row mrow_a stores only columns [ma0, ma1), row mrow_b only
     // [mb0, mb1).
-    __device__ __forceinline__ static uint32_t seg(const RunArgs &a, const Inst &I, const double *mp, int xt,
-                                                   int y0, int y1, int mrow_a, int ma0, int ma1, int mrow_b,
-                                                   int mb0, int mb1, int s, int64_t step, int lane)
+    __device__ __forceinline__ static uint32_t seg(const RunArgs &a, const Inst &I, const double *mp,
+                                                   const Bufs &B, double *jbuf, int xt, int y0, int y1,
+                                                   int mrow_a, int ma0, int ma1, int mrow_b, int mb0, int mb1,
+                                                   int s, int64_t step, int lane)
     {
         const int nx = I.nx, ny = I.ny, bc = a.bc;
         const int64_t plane = (int64_t)nx * ny;
 
-        double *blk = a.ws + I.ws_off;
+        double *blk = B.blk;
         double *zb = blk;
         double *acc = blk + NV * plane;
         double *Ya = blk + 2 * NV * plane;
         double *Yb = blk + 3 * NV * plane;
-        const double *zin = a.z_in + I.off;
-        double *zout = a.z_out + I.off;
+        const double *zin = B.zin;
+        double *zout = B.zout;
         const double *src = (step == 0) ? zin : ((((step - 1) + a.parity) & 1) == 0 ? zout : zb);
         double *dst = (((step + a.parity) & 1) == 0) ? zout : zb;
         const double *Yin = (s == 0) ? src : ((s & 1) ? Ya : Yb);
         double *Ynext = (s & 1) ? Yb : Ya;
+        if (B.store != nullptr) {
+            const int64_t S = NV * plane;
+            src = B.store + step * NS * S;
+            dst = B.store + (step + 1) * NS * S;
+            Yin = B.store + (step * NS + s) * S;
+            Ynext = B.store + (step * NS + s + 1) * S;
+        }
         const bool last = (s == NS - 1);
         const double ca = a.cacc[s];
         const double cyv = last ? 0.0 : a.cy[s];
@@ -339,46 +532,55 @@ struct Stepper {
 
             // local terms (centre weight folded in)
             double F[CX][NV];
+            const int64_t ro_j = (int64_t)y * nx;
+            if constexpr (KIND == KIND_PRIMAL) {
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                double t[NV];
-                MD::local(coef, mp, zc[c], t);
+                for (int c = 0; c < CX; ++c) {
+                    double t[NV];
+                    MD::local(coef, mp, zc[c], t);
 #pragma unroll
-                for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+                    for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+                }
+            } else if constexpr (KIND == KIND_PRIMAL_J) {
+                double Jv[NJ > 0 ? NJ : 1][CX];
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    double t[NV], J[NJ > 0 ? NJ : 1];
+                    MD::local_jac(coef, mp, zc[c], t, J);
+#pragma unroll
+                    for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) Jv[j][c] = J[j];
+                }
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) store_row(jbuf + j * plane + ro_j, x0, vin, in_grid, Jv[j]);
+            } else {
+                double Jv[NJ > 0 ? NJ : 1][CX];
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    double dummy;
+                    load_row(jbuf + j * plane, nx, y, cx, hx, vin, false, Jv[j], dummy);
+                }
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    double t[NV], J[NJ > 0 ? NJ : 1];
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) J[j] = Jv[j][c];
+                    MD::tan_local(coef, mp, J, zc[c], t);
+#pragma unroll
+                    for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+                }
             }
 
             // off-centre stencil sums of the diffusive fields
 #pragma unroll
             for (int f = 0; f < ND; ++f) {
-                double up = __shfl_up_sync(CG_FULL, mid[f][CX - 1], 1);
-                double dn = __shfl_down_sync(CG_FULL, mid[f][0], 1);
-                if (lane == 0) up = hmid[f];
-                if (lane == 31) dn = hmid[f];
-                double V[CX];
+                double Ff[CX];
 #pragma unroll
-                for (int c = 0; c < CX; ++c) V[c] = lo[f][c] + hi[f][c];
-                double Vl = 0.0, Vr = 0.0;
-                if (ST == CG_STENCIL9) {
-                    const double Vh = hlo[f] + hhi[f];
-                    Vl = __shfl_up_sync(CG_FULL, V[CX - 1], 1);
-                    Vr = __shfl_down_sync(CG_FULL, V[0], 1);
-                    if (lane == 0) Vl = Vh;
-                    if (lane == 31) Vr = Vh;
-                }
+                for (int c = 0; c < CX; ++c) Ff[c] = F[c][f];
+                add_offcentre<ST, CX>(lane, lo[f], mid[f], hi[f], hlo[f], hmid[f], hhi[f], wx[f], wy[f], wd[f], Ff);
 #pragma unroll
-                for (int c = 0; c < CX; ++c) {
-                    const double W = (c == 0) ? up : mid[f][c - 1];
-                    const double E = (c == CX - 1) ? dn : mid[f][c + 1];
-                    double acc_f = F[c][f];
-                    if (ST == CG_STENCIL9) {
-                        const double VW = (c == 0) ? Vl : V[c - 1];
-                        const double VE = (c == CX - 1) ? Vr : V[c + 1];
-                        acc_f = fma(wd[f], VW + VE, acc_f);
-                    }
-                    acc_f = fma(wy[f], V[c], acc_f);
-                    acc_f = fma(wx[f], W + E, acc_f);
-                    F[c][f] = acc_f;
-                }
+                for (int c = 0; c < CX; ++c) F[c][f] = Ff[c];
             }
 
             // Runge-Kutta combine and stores
@@ -439,7 +641,8 @@ struct Stepper {
         const int tx = lt % I.tiles_x, ty = lt / I.tiles_x;
         const int y0 = ty * a.rows;
         const int y1 = min(y0 + a.rows, I.ny) - 1;
-        return seg(a, I, mp, tx * 32 * CX, y0, y1, -1, 0, 0, -1, 0, 0, s, step, lane);
+        const Bufs B{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, a.store};
+        return seg(a, I, mp, B, nullptr, tx * 32 * CX, y0, y1, -1, 0, 0, -1, 0, 0, s, step, lane);
     }
 };
 
@@ -469,7 +672,9 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
         for (int k = sbeg; k < send; ++k) {
             const Seg sg = a.segs[k];
             const Inst &I = a.inst[sg.inst];
-            bad |= S::seg(a, I, mp, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b, sg.mb0, sg.mb1,
+            const Bufs B{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, a.store};
+            bad |= S::seg(a, I, mp, B, nullptr, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
+                          sg.mb0, sg.mb1,
                           s, step, lane);
         }
     };
