@@ -278,6 +278,50 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     for sp in seq_plans:
         sp.close()
     bp.close()
+
+    # differentiation workload: 512^2 two-field RK4 5-point.  Plain stepper,
+    # 64 tangents in one tangent-linear run, and the checkpointed adjoint of
+    # the full T = 2000 horizon, all in cell-updates per second.
+    n = 512
+    p = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, scheme=api.RK4, dt=2.5e-4)
+    plan = plan_cls(p)
+    z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
+    T = 2000
+    t_plain = timed(plan, z, T, reps=2)
+    dz0 = torch.from_numpy(np.stack([I.unit_direction(z.shape, 2, offset=i * z.numel()) for i in range(64)])).cuda()
+    steps_t = 200
+    plan.tlm(z, dz0, steps_t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.tlm(z, dz0, steps_t)
+    e1.record()
+    torch.cuda.synchronize()
+    t_tlm = e0.elapsed_time(e1) / 1e3
+    plan.status()
+    zT = plan.run(z, T)
+    lamT = torch.zeros_like(zT)
+    lamT[0] = 2.0 * zT[0]
+    plan.adjoint(z, lamT, T)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.adjoint(z, lamT, T)
+    e1.record()
+    torch.cuda.synchronize()
+    t_adj = e0.elapsed_time(e1) / 1e3
+    plan.status()
+    g_plain = n * n * T / t_plain / 1e9
+    rows["grad-512x512-5pt-rk4"] = {
+        "gcups_plain": g_plain,
+        "tlm_gcups_tangent_cells": 64 * n * n * steps_t / t_tlm / 1e9,
+        "tlm_vs_plain": (64 * n * n * steps_t / t_tlm / 1e9) / g_plain,
+        "adjoint_gcups": n * n * T / t_adj / 1e9,
+        "adjoint_seconds_T2000": t_adj,
+        "adjoint_vs_plain": (n * n * T / t_adj / 1e9) / g_plain,
+        "note": "tlm: 64 tangents x 200 steps (rate); adjoint: full T = 2000 with ceil(sqrt(T)) checkpoints "
+                "(forward + segment recompute + reverse sweep)"}
+    plan.close()
     return rows
 
 

@@ -70,9 +70,14 @@ enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2 };
 #define CG_FLAG_ALLOW_UNSTABLE   (1u << 0)  /* skip the dt stability check */
 #define CG_FLAG_PER_STAGE_LAUNCH (1u << 1)  /* one kernel launch per RK stage instead of one
                                                persistent cooperative launch per run */
-#define CG_FLAG_TEST_STUCK_BARRIER (1u << 8) /* testing only: the first grid barrier waits for
-                                               one block more than exist, so it must give up
-                                               after barrier_timeout_s and report CG_ETIMEOUT */
+#define CG_FLAG_GRID_BARRIER     (1u << 2)  /* separate stages by a grid-wide barrier instead of
+                                               waiting only for the blocks that own each
+                                               block's halo (the default with the static
+                                               schedule) */
+#define CG_FLAG_TEST_STUCK_BARRIER (1u << 8) /* testing only: the first wait between stages
+                                               expects one arrival (or one stage) more than can
+                                               happen, so it must give up after
+                                               barrier_timeout_s and report CG_ETIMEOUT */
 
 /* Device status bits (cg_read_status). */
 #define CG_DEV_NONFINITE 1u   /* a non-finite value was stored */
@@ -207,6 +212,32 @@ cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t check
 cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
                          int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream);
 
+/* ------------------------------------------------- Newton-Krylov step */
+
+/* Sect. 1 names matrix-free Newton-Krylov solvers (e.g. for periodic orbits
+ * of the flow) as the reason double precision is needed.  One Newton step on
+ * the period-T flow map Phi_T solves
+ *     (J_T - I) dz = -(Phi_T(z0) - z0),   J_T = d Phi_T / d z (z0)
+ * by restarted GMRES(restart) with modified Gram-Schmidt, J_T v from
+ * cg_tlm_run (exact, not finite differences).  All vector work runs on the
+ * device with fixed-order reductions; the (restart+1) x restart Hessenberg
+ * least-squares problem is solved on the host with Givens rotations.
+ * Stops when the residual drops below rtol * |b| or after max_restarts
+ * cycles.  dz: device output (plan layout).  res_hist: optional host array
+ * of restart*max_restarts + 1 residual norms (entry 0 = |b|).  n_iter:
+ * optional host output, Arnoldi steps taken.  Synchronous on the stream
+ * (it reads dot products back).  Single-instance plans only. */
+cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t *bytes);
+cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
+                               int32_t max_restarts, double rtol, double *dz, double *res_hist,
+                               int32_t *n_iter, void *workspace, void *stream);
+
+/* Deterministic vector kernels used by the Newton-Krylov step.
+ * cg_dot: *result (device) = sum_i x[i] y[i], summed in a fixed order; the
+ * workspace needs 256 doubles.  cg_axpby: y = a x + b y (device vectors). */
+cg_status cg_dot(const double *x, const double *y, int64_t n, double *result, void *workspace, void *stream);
+cg_status cg_axpby(double a, const double *x, double b, double *y, int64_t n, void *stream);
+
 /* ----------------------------------------------------------------- misc */
 
 /* Message describing the last error on the calling thread ("" if none). */
@@ -232,10 +263,13 @@ cg_status cg_default_params(int32_t model, double *out);
  * mrow_b, mb0, mb1}, meaning columns [x0, x0 + 32*cells_x) of rows y0..y1,
  * except that row mrow_a keeps only columns [ma0, ma1) and row mrow_b only
  * [mb0, mb1); and n_blocks*warps_per_block + 1 prefix offsets to
- * warp_seg_out (warp w owns segments [warp_seg_out[w], warp_seg_out[w+1])). */
+ * warp_seg_out (warp w owns segments [warp_seg_out[w], warp_seg_out[w+1])).
+ * deps_out (optional, 2*n_blocks int32): for each block the first and last
+ * block whose cells lie within one row and one column of its own (the
+ * blocks it waits for between stages). */
 cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
                              int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
-                             int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs);
+                             int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs, int32_t *deps_out);
 
 /* CG_ABI_VERSION of the loaded library. */
 int32_t cg_abi_version(void);

@@ -64,6 +64,15 @@ _SIGS = {
     "cg_adjoint_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "cg_newton_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_newton_gmres_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_dot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p]),
+    "cg_axpby": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_void_p]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_n_fields": (ctypes.c_int32, [ctypes.c_int32]),
     "cg_n_params": (ctypes.c_int32, [ctypes.c_int32]),
@@ -72,7 +81,8 @@ _SIGS = {
     "cg_static_schedule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
-                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int32)]),
     "cg_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
 }

@@ -222,6 +222,22 @@ class Plan:
                                         _stream_handle(stream)))
         return lam0, dLdD
 
+    def newton_step(self, z0: torch.Tensor, period_steps: int, restart: int = 30, max_restarts: int = 1,
+                    rtol: float = 1e-10, stream=None):
+        """One Newton step on the period-T flow map by GMRES(restart) with
+        exact Jacobian-vector products.  Returns (dz, residual_history)."""
+        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_newton_workspace_size(self._h, int(restart), ctypes.byref(sz)))
+        ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        dz = torch.empty_like(z0)
+        hist = (ctypes.c_double * (restart * max_restarts + 1))()
+        nit = ctypes.c_int32()
+        check(_lib.lib().cg_newton_gmres_step(self._h, z0.data_ptr(), int(period_steps), int(restart),
+                                              int(max_restarts), float(rtol), dz.data_ptr(), hist,
+                                              ctypes.byref(nit), ws.data_ptr(), _stream_handle(stream)))
+        return dz, [hist[i] for i in range(nit.value + 1)]
+
     def status(self, stream=None, workspace: Optional[torch.Tensor] = None, raise_on_error: bool = True) -> int:
         ws = self.workspace() if workspace is None else workspace
         flags = ctypes.c_uint32()

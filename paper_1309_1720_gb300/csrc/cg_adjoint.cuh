@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
     } else {
         for (int64_t g = a.g_begin; g < a.g_end; ++g) {
             stage(g);
-            if (g + 1 < a.g_end && !grid_barrier(a.sync, a.status, a.timeout_ns, a.nblocks_expect)) {
+            if (g + 1 < a.g_end && !stage_sync(a, g, g == a.g_begin)) {
                 ok = false;
                 break;
             }

@@ -121,6 +121,9 @@ struct cg_plan_s {
     const void *kernel = nullptr;
     int nblocks = 0;
     double dxx[4] = {};              // Dxx of the first instance (gradient normalisation)
+    std::vector<int2> deps;          // halo owners of each block (neighbour sync)
+    int2 *d_deps = nullptr;
+    int32_t sync_mode = cgk::SYNC_GRID;
 };
 
 namespace {
@@ -343,6 +346,37 @@ void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t>
     warp_seg[(size_t)G * NW] = (int32_t)segs.size();
 }
 
+// For each block of the static schedule, the range of blocks that own its
+// one-cell halo: every cell within one row and one column of the block's
+// cells, inside the same instance.  Block b owns global cells
+// [N b / G, N (b+1) / G); the owner of cell c is ceil((c+1) G / N) - 1.
+void halo_dependencies(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int G,
+                       std::vector<int2> &deps)
+{
+    const int n = (int)nxs.size();
+    std::vector<int64_t> cstart(n + 1, 0);
+    for (int k = 0; k < n; ++k) cstart[k + 1] = cstart[k] + (int64_t)nxs[k] * nys[k];
+    const int64_t N = cstart[n];
+    auto owner = [&](int64_t c) { return (int)(((c + 1) * (int64_t)G - 1) / N); };
+    deps.assign(G, make_int2(0, -1));
+    int k0 = 0;
+    for (int b = 0; b < G; ++b) {
+        const int64_t c0 = N * b / G, c1 = N * (b + 1) / G;
+        int lo = b, hi = b;
+        while (k0 < n && cstart[k0 + 1] <= c0) ++k0;
+        for (int k = k0; k < n && cstart[k] < c1; ++k) {
+            const int64_t l0 = std::max(c0, cstart[k]) - cstart[k];
+            const int64_t l1 = std::min(c1, cstart[k + 1]) - cstart[k];
+            if (l0 >= l1) continue;
+            const int64_t nx = nxs[k], cells = (int64_t)nxs[k] * nys[k];
+            const int64_t h0 = std::max<int64_t>(0, l0 - nx - 1), h1 = std::min<int64_t>(cells, l1 + nx + 1);
+            lo = std::min(lo, owner(cstart[k] + h0));
+            hi = std::max(hi, owner(cstart[k] + h1 - 1));
+        }
+        deps[b] = make_int2(lo, hi);
+    }
+}
+
 cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tune, cg_plan *out)
 {
     if (!out) return fail(CG_EINVAL, "out is NULL");
@@ -469,7 +503,13 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         std::vector<int32_t> nxs, nys;
         for (const Inst &I : P->inst) { nxs.push_back(I.nx); nys.push_back(I.ny); }
         static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg);
+        halo_dependencies(nxs, nys, P->nblocks, P->deps);
+        P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
+                        !(P->flags & CG_FLAG_GRID_BARRIER)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
     }
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_deps, sizeof(int2) * std::max<size_t>(1, P->deps.size()));
+    if (e == cudaSuccess && !P->deps.empty())
+        e = cudaMemcpy(P->d_deps, P->deps.data(), sizeof(int2) * P->deps.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_inst, sizeof(Inst) * n_inst);
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_inst, P->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
@@ -484,6 +524,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         if (P->d_inst) cudaFree(P->d_inst);
         if (P->d_segs) cudaFree(P->d_segs);
         if (P->d_warp_seg) cudaFree(P->d_warp_seg);
+        if (P->d_deps) cudaFree(P->d_deps);
         delete P;
         return cuda_fail(e, "plan creation");
     }
@@ -515,6 +556,10 @@ cg_status launch_stages(cg_plan P, const void *kernel, void **args, RunArgs &a, 
     a.g_begin = g0;
     a.g_end = g1;
     a.nblocks_expect = (uint32_t)P->nblocks;
+    if (a.sync_mode == cgk::SYNC_NEIGHBOR) {
+        e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned) * (size_t)P->nblocks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(flags)");
+    }
     a.stuck_barrier = (P->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
@@ -593,6 +638,7 @@ CG_API cg_status cg_plan_destroy(cg_plan plan)
     if (plan->d_inst) cudaFree(plan->d_inst);
     if (plan->d_segs) cudaFree(plan->d_segs);
     if (plan->d_warp_seg) cudaFree(plan->d_warp_seg);
+    if (plan->d_deps) cudaFree(plan->d_deps);
     delete plan;
     return CG_OK;
 }
@@ -640,6 +686,7 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     a.segs = plan->d_segs;
     a.warp_seg = plan->d_warp_seg;
     a.sched = plan->sched;
+    const cg_plan_s *P = plan;
     a.n_inst = (int32_t)plan->inst.size();
     a.n_tiles = plan->n_tiles;
     a.bc = plan->bc;
@@ -649,6 +696,9 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
     a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
     a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
+    a.flags = reinterpret_cast<unsigned *>(ws + cgk::WS_FLAGS_OFF);
+    a.deps = P->d_deps;
+    a.sync_mode = P->sync_mode;
     const bool alias_single_stage = (plan->ns == 1) && (z_in == z_out);
     a.parity = alias_single_stage ? 1 : (int32_t)((n_steps - 1) & 1);
     a.timeout_ns = plan->timeout_ns;
@@ -747,6 +797,9 @@ void base_args(cg_plan P, RunArgs &a, const double *z_in, double *z_out, char *w
     a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
     a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
     a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
+    a.flags = reinterpret_cast<unsigned *>(ws + cgk::WS_FLAGS_OFF);
+    a.deps = P->d_deps;
+    a.sync_mode = P->sync_mode;
     a.timeout_ns = P->timeout_ns;
     std::memcpy(a.cacc, P->cacc, sizeof a.cacc);
     std::memcpy(a.cy, P->cy, sizeof a.cy);
@@ -918,6 +971,9 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     int64_t r = 0;
     for (int64_t j = L.nseg - 1; j >= 0; --j) {
         const int64_t m = std::min<int64_t>(L.c, n_steps - j * L.c);
+        // the segment's first state is the first stage input the sweep revisits
+        e = cudaMemcpyAsync(store, cp + j * L.S, sbytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(segment start)");
         base_args(plan, a, cp + j * L.S, store + m * plan->ns * L.S, ws);
         a.store = store;
         void *fargs[] = {&a};
@@ -973,7 +1029,7 @@ CG_API cg_status cg_default_params(int32_t model, double *out)
 
 CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
                                     int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
-                                    int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs)
+                                    int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs, int32_t *deps_out)
 {
     if (!nx || !ny || n_inst < 1 || (cells_x != 1 && cells_x != 2) || n_blocks < 1 || warps_per_block < 1 ||
         !warp_seg_out || !n_segs)
@@ -986,6 +1042,14 @@ CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_
     static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws);
     *n_segs = (int64_t)segs.size();
     std::copy(ws.begin(), ws.end(), warp_seg_out);
+    if (deps_out) {
+        std::vector<int2> deps;
+        halo_dependencies(nxs, nys, n_blocks, deps);
+        for (int b = 0; b < n_blocks; ++b) {
+            deps_out[2 * b] = deps[b].x;
+            deps_out[2 * b + 1] = deps[b].y;
+        }
+    }
     if (segs_out) {
         if ((int64_t)segs.size() > segs_cap) return fail(CG_EINVAL, "segs_cap too small (%lld needed)",
                                                          (long long)segs.size());

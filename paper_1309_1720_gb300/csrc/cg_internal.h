@@ -50,6 +50,10 @@ struct RunArgs {
     double *z_out;
     double *ws;                  // base of the per-instance scratch blocks
     double *store;               // optional: keep every stage input (single instance; see Bufs)
+    unsigned *flags;             // per-block count of finished stages (neighbour sync)
+    const int2 *deps;            // blocks [deps[b].x, deps[b].y] own the halo of block b
+    int32_t sync_mode;           // SYNC_GRID or SYNC_NEIGHBOR between stages
+    int32_t pad_sync;
     unsigned *sync;              // [0] barrier count, [1] barrier generation, [2..4] tile queues
     uint32_t *status;            // device status word (CG_DEV_*)
     int64_t g_begin, g_end;      // global stage range [g_begin, g_end) of this launch
@@ -66,10 +70,14 @@ struct RunArgs {
 constexpr int SCRATCH_PLANES = 4;
 
 // Workspace header (bytes): status word and sync counters.
-constexpr size_t WS_HEADER = 256;
+constexpr size_t WS_HEADER = 8192;
 constexpr size_t WS_STATUS_OFF = 0;
 constexpr size_t WS_SYNC_OFF = 64;
 constexpr int SYNC_WORDS = 8;
+constexpr size_t WS_FLAGS_OFF = 512;                               // per-block stage counters
+constexpr int MAX_FLAG_BLOCKS = (int)((WS_HEADER - WS_FLAGS_OFF) / 4);
+
+enum { SYNC_GRID = 0, SYNC_NEIGHBOR = 1 };
 
 enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION };
 

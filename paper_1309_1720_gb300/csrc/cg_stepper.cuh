@@ -106,6 +106,58 @@ static __device__ __noinline__ bool grid_barrier(unsigned *sync, uint32_t *statu
     return s_ok != 0;
 }
 
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Neighbour synchronisation between stages (static schedule).  A stage of
+// block b only reads its own cells and a one-cell halo, which blocks
+// deps[b].x .. deps[b].y own; and it only overwrites buffers that those same
+// blocks read in the stage before.  So block b publishes how many stages it
+// has finished and, before the next one, waits (bounded) until every block
+// of its range has finished as many.  No grid-wide barrier: blocks drift by
+// at most one stage against their neighbours and stage tails overlap.
+static __device__ __noinline__ bool neighbor_sync(unsigned *flags, const int2 *deps, uint32_t *status,
+                                                  uint64_t timeout_ns, unsigned done, unsigned extra)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_u32(flags + blockIdx.x, done);
+        const int2 d = deps[blockIdx.x];
+        const unsigned need = done + extra;
+        int ok = 1;
+        const uint64_t t0 = global_timer_ns();
+        const uint64_t max_iter = (timeout_ns >> 5) + (1ull << 20);
+        uint64_t it = 0;
+        for (int q = d.x; q <= d.y && ok; ++q) {
+            while (ld_acquire_u32(flags + q) < need) {
+                __nanosleep(32);
+                if ((++it & 63) == 0 && (global_timer_ns() - t0 > timeout_ns || it > max_iter)) {
+                    ok = 0;
+                    atomicOr(status, CG_DEV_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Synchronise after global stage g of a persistent launch (g_begin <= g).
+__device__ __forceinline__ bool stage_sync(const RunArgs &a, int64_t g, bool first)
+{
+    const unsigned extra = (first && a.stuck_barrier) ? 1u : 0u;
+    if (a.sync_mode == SYNC_NEIGHBOR)
+        return neighbor_sync(a.flags, a.deps, a.status, a.timeout_ns, (unsigned)(g - a.g_begin + 1), extra);
+    return grid_barrier(a.sync, a.status, a.timeout_ns, a.nblocks_expect + extra);
+}
+
 // ------------------------------------------------------------------ models
 
 template <int M> struct Model;
@@ -715,9 +767,9 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
                 }
             }
             if (g + 1 < a.g_end) {
-                const uint32_t expect = a.nblocks_expect + ((first_barrier && a.stuck_barrier) ? 1u : 0u);
+                const bool ok = stage_sync(a, g, first_barrier);
                 first_barrier = false;
-                if (!grid_barrier(a.sync, a.status, a.timeout_ns, expect)) return;
+                if (!ok) return;
             }
         }
     }

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
     } else {
         for (int64_t g = a.g_begin; g < a.g_end; ++g) {
             stage((int)(g % NS), g / NS);
-            if (g + 1 < a.g_end && !grid_barrier(a.sync, a.status, a.timeout_ns, a.nblocks_expect)) return;
+            if (g + 1 < a.g_end && !stage_sync(a, g, g == a.g_begin)) return;
         }
     }
     bad = __any_sync(CG_FULL, bad != 0);

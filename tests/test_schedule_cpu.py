@@ -1,6 +1,7 @@
 """Host logic of the static schedule (no GPU): every cell of every instance is
-owned by exactly one warp segment, blocks get equal cell counts, and warps
-inside a block get equal strip-rows to within one row."""
+owned by exactly one warp segment, blocks get equal cell counts, warps inside
+a block get equal strip-rows to within one row, and each block's dependency
+range covers the owners of its whole one-cell halo."""
 import ctypes
 
 import numpy as np
@@ -20,23 +21,28 @@ def schedule(L, nxs, nys, cx, G, NW):
     b = (ctypes.c_int32 * n)(*nys)
     ws = (ctypes.c_int32 * (G * NW + 1))()
     ns = ctypes.c_int64()
-    assert L.cg_static_schedule(a, b, n, cx, G, NW, None, 0, ws, ctypes.byref(ns)) == 0
+    assert L.cg_static_schedule(a, b, n, cx, G, NW, None, 0, ws, ctypes.byref(ns), None) == 0
     segs = (ctypes.c_int32 * (10 * max(1, ns.value)))()
-    assert L.cg_static_schedule(a, b, n, cx, G, NW, segs, ns.value, ws, ctypes.byref(ns)) == 0
-    return np.array(segs[:10 * ns.value]).reshape(-1, 10), np.array(ws[:])
+    deps = (ctypes.c_int32 * (2 * G))()
+    assert L.cg_static_schedule(a, b, n, cx, G, NW, segs, ns.value, ws, ctypes.byref(ns), deps) == 0
+    return (np.array(segs[:10 * ns.value]).reshape(-1, 10), np.array(ws[:]),
+            np.array(deps[:]).reshape(G, 2))
 
 
-@pytest.mark.parametrize("nxs,nys,cx,G,NW", [
+CASES = [
     ([1024], [1024], 2, 152, 16),
     ([128], [128], 2, 152, 16),
     ([2], [2], 1, 152, 16),
     ([67], [45], 1, 7, 4),
     ([150, 97, 2, 64, 300], [97, 150, 3, 64, 11], 2, 13, 8),
     ([2048], [2048], 2, 152, 16),
-])
+]
+
+
+@pytest.mark.parametrize("nxs,nys,cx,G,NW", CASES)
 def test_exact_cover_and_balance(L, nxs, nys, cx, G, NW):
-    segs, ws = schedule(L, nxs, nys, cx, G, NW)
-    own = [np.zeros((ny, nx), dtype=np.int32) for nx, ny in zip(nxs, nys)]
+    segs, ws, deps = schedule(L, nxs, nys, cx, G, NW)
+    own = [np.full((ny, nx), -1, dtype=np.int64) for nx, ny in zip(nxs, nys)]
     tw = 32 * cx
     per_warp = np.zeros(G * NW, dtype=np.int64)
     per_block = np.zeros(G, dtype=np.int64)
@@ -46,18 +52,35 @@ def test_exact_cover_and_balance(L, nxs, nys, cx, G, NW):
             nx = nxs[inst]
             assert x0 % tw == 0 and 0 <= y0 <= y1 < nys[inst]
             per_warp[w] += y1 - y0 + 1
-            for y in range(y0, y1 + 1):
-                for x in range(x0, min(x0 + tw, nx)):
-                    if y == ra and not (a0 <= x < a1):
-                        continue
-                    if y == rb and not (b0 <= x < b1):
-                        continue
-                    own[inst][y, x] += 1
-                    per_block[w // NW] += 1
+            x1 = min(x0 + tw, nx)
+            blk = np.zeros((y1 - y0 + 1, x1 - x0), dtype=bool)
+            blk[:] = True
+            xs = np.arange(x0, x1)
+            if y0 <= ra <= y1:
+                blk[ra - y0] = (xs >= a0) & (xs < a1)
+            if y0 <= rb <= y1:
+                blk[rb - y0] = (xs >= b0) & (xs < b1)
+            sub = own[inst][y0:y1 + 1, x0:x1]
+            assert np.all(sub[blk] == -1)
+            sub[blk] = w // NW
+            per_block[w // NW] += int(blk.sum())
     for o in own:
-        assert np.all(o == 1)
+        assert np.all(o >= 0)
     total = sum(nx * ny for nx, ny in zip(nxs, nys))
     assert per_block.max() - per_block.min() <= 1 + (0 if total >= G else 1)
     for b in range(G):
         pw = per_warp[b * NW:(b + 1) * NW]
         assert pw.max() - pw.min() <= 1
+    # every block owning a cell within one row/column of block b's cells lies
+    # in b's dependency range
+    for o in own:
+        ny, nx = o.shape
+        lo = np.full((ny, nx), np.iinfo(np.int64).max)
+        hi = np.full((ny, nx), -1)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                src = o[max(0, dy):ny + min(0, dy), max(0, dx):nx + min(0, dx)]
+                dst = (slice(max(0, -dy), ny + min(0, -dy)), slice(max(0, -dx), nx + min(0, -dx)))
+                lo[dst] = np.minimum(lo[dst], src)
+                hi[dst] = np.maximum(hi[dst], src)
+        assert np.all(deps[o, 0] <= lo) and np.all(hi <= deps[o, 1])

@@ -63,9 +63,14 @@ def test_tlm_fd_full_size(cuda_ok):
     zd = torch.from_numpy(z0).cuda()
     _, dzT = plan.tlm(zd, torch.from_numpy(dz0).cuda(), steps)
     plan.status()
-    eps = 1e-6
-    for i in (0, 63):
-        d = torch.from_numpy(dz0[i]).cuda()
-        fd = (plan.run(zd + eps * d, steps) - plan.run(zd - eps * d, steps)) / (2 * eps)
-        err = torch.linalg.norm(dzT[i] - fd) / torch.linalg.norm(fd)
-        assert float(err) <= 1e-8, (i, float(err))
+    # Central differences of a 524288-dimensional state: each run carries
+    # ~1e-15 of rounding per cell, so at eps = 1e-6 the difference quotient
+    # has a noise floor of ~1e-15/2e-6 * sqrt(N) ~ 4e-7 in the relative
+    # 2-norm; at eps = 1e-4 the floor is ~4e-9 and the O(eps^2) truncation is
+    # far smaller, so that is where the 1e-8 bound is checked.
+    for eps, tol in ((1e-6, 2e-6), (1e-4, 1e-8)):
+        for i in (0, 63):
+            d = torch.from_numpy(dz0[i]).cuda()
+            fd = (plan.run(zd + eps * d, steps) - plan.run(zd - eps * d, steps)) / (2 * eps)
+            err = torch.linalg.norm(dzT[i] - fd) / torch.linalg.norm(fd)
+            assert float(err) <= tol, (eps, i, float(err))
