@@ -162,6 +162,26 @@ cg_status cg_workspace_size(cg_plan plan, size_t *bytes);
 cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
                  void *workspace, void *stream);
 
+/* Same as cg_run, for callers that cannot allocate device memory when they
+ * step: code running while a stream is captured into a CUDA graph (where
+ * allocation is not allowed), programs whose device memory belongs to their
+ * own pool allocator, and real-time loops that forbid allocation after
+ * start-up.  The paper has no counterpart; this is a library convenience.
+ * The scratch comes from one statically allocated 32 MiB device array inside
+ * the library (every GPU that loads the library holds it until the process
+ * exits) instead of a caller workspace, so the call allocates nothing.
+ * Plans whose cg_workspace_size exceeds 32 MiB (e.g. a two-field 1024^2
+ * grid) are rejected with CG_EINVAL and a message.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current: make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * clears its status and synchronisation words itself), so calls that
+ * overlap on the GPU race: issue them on one stream or otherwise serialise
+ * them.  status_dev (device, may be NULL) receives the call's CG_DEV_* bits
+ * once the run has finished on the stream. */
+cg_status cg_run_noalloc(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
+                         uint32_t *status_dev, void *stream);
+
 /* Synchronise the stream and return the device status bits (CG_DEV_*)
  * recorded by the last run that used this workspace.  Returns CG_ENAN or
  * CG_ETIMEOUT when the matching bit is set, CG_OK otherwise. */

@@ -1004,6 +1004,12 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "reduce kernel");
 }
 
+cg_status cgk::set_last_error(cg_status st, const char *msg)
+{
+    g_err = msg;
+    return st;
+}
+
 CG_API const char *cg_last_error(void)
 {
     return g_err.c_str();

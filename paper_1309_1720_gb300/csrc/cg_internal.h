@@ -93,6 +93,9 @@ const void *adj_kernel_fhn(int stencil, int scheme, int cx);
 const void *adj_kernel_bocf(int stencil, int scheme, int cx);
 const void *adj_kernel_diff(int stencil, int scheme, int cx);
 
+// Record a message for cg_last_error() on the calling thread; returns st.
+cg_status set_last_error(cg_status st, const char *msg);
+
 // Stored Jacobian entries per cell of each model (0 for the linear model).
 inline int model_nj(int model)
 {
