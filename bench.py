@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run 20 steps of the workload twice and exit (for ncu captures)")
+    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None, choices=["fhn", "bocf"],
+                    help="run a short case twice and exit (for ncu captures): 20 steps of the "
+                         "1024^2 workload (fhn) or 2 steps of the 2048^2 four-field model (bocf)")
     return ap.parse_args()
 
 
@@ -340,15 +341,33 @@ def main():
 
     prob = api.Problem(model=api.FHN, nx=NX, ny=NY, dx=0.04, stencil=api.STENCIL9, alpha_d=1 / 6,
                        scheme=api.RK4, dt=DT)
-    plan = Plan(prob)
     z0_host = I.fhn_broken_wave(NX, NY, seed=0)
     z0 = torch.from_numpy(z0_host).cuda()
+    tuning = None
+    if args.profile_case:
+        plan = Plan(prob)
+    else:
+        # launch shape chosen by the project's autotuner on a short run of the
+        # same workload (cached per GPU / model / size class)
+        from paper_1309_1720_gb300 import autotune
+        tuning = autotune.tune([prob], z0, n_steps=200)
+        plan = autotune.tuned_plan([prob], z0, n_steps=200)
     out = torch.empty_like(z0)
     ws_t = plan.workspace()
 
     if args.profile_case:
+        if args.profile_case == "bocf":
+            # four-field 2048^2 anisotropic 9-point RK4: 640 MB working set
+            n = 2048
+            plan = Plan(api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
+                                    stencil=api.STENCIL9, scheme=api.RK4, dt=0.05))
+            z0 = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
+            out = torch.empty_like(z0)
+            steps = 2
+        else:
+            steps = 20
         for _ in range(2):
-            plan.run(z0, 20, out=out)
+            plan.run(z0, steps, out=out)
         plan.status()
         torch.cuda.synchronize()
         print("profile case done")
@@ -437,7 +456,7 @@ def main():
                                         "256 threads x 4 blocks/SM), FMA = 2 flops",
                          "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
                          "hbm_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
-                         "kernel": "k_stage<FHN, 9-point, RK4, 2 cells/lane> (persistent)"},
+                         "kernel": "k_stage<FHN, 9-point, RK4> (persistent)", "tuning": tuning},
             "e2e": {"value": ws * cells * args.steps / e2e_tot / 1e9, "unit": "GCUPS",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps,

@@ -70,10 +70,10 @@ enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2 };
 #define CG_FLAG_ALLOW_UNSTABLE   (1u << 0)  /* skip the dt stability check */
 #define CG_FLAG_PER_STAGE_LAUNCH (1u << 1)  /* one kernel launch per RK stage instead of one
                                                persistent cooperative launch per run */
-#define CG_FLAG_GRID_BARRIER     (1u << 2)  /* separate stages by a grid-wide barrier instead of
-                                               waiting only for the blocks that own each
-                                               block's halo (the default with the static
-                                               schedule) */
+#define CG_FLAG_NEIGHBOR_SYNC    (1u << 2)  /* static schedule only: between stages each block
+                                               waits for the blocks that own its halo instead of
+                                               a grid-wide barrier (measured slower on GB300 for
+                                               the configurations here; an autotuner option) */
 #define CG_FLAG_TEST_STUCK_BARRIER (1u << 8) /* testing only: the first wait between stages
                                                expects one arrival (or one stage) more than can
                                                happen, so it must give up after

@@ -36,6 +36,14 @@ enum {
  * clocks have ramped).  Synchronous. */
 cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per_s, double *seconds);
 
+/* Evaluate the library's own FP64 elementary functions on the device beside
+ * CUDA's, for verification: fn 0 = reciprocal 1/x (x positive, normal, within
+ * single-precision exponent range), fn 1 = e^x for x <= 0 (table-driven, after
+ * Tang 1989), fn 2 = sigmoid 1/(1 + e^-x).  own[i] gets the library's value,
+ * ref[i] CUDA's (1.0/x, exp(x), (1 + tanh(x/2))/2).  x, own, ref: device
+ * arrays of n doubles.  Synchronous. */
+cg_status cg_check_fastmath(int32_t fn, const double *x, double *own, double *ref, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,7 +9,7 @@ hand-written CUDA kernels for sm_103a behind a C ABI
 """
 from .api import (  # noqa: F401
     ABI_VERSION, BOCF, CLAMP, DIFFUSION, EULER, FHN, HEUN, KARMA, MIRROR, RK4,
-    STENCIL5, STENCIL9, FLAG_ALLOW_UNSTABLE, FLAG_PER_STAGE_LAUNCH, FLAG_TEST_STUCK_BARRIER,
+    STENCIL5, STENCIL9, FLAG_ALLOW_UNSTABLE, FLAG_PER_STAGE_LAUNCH, FLAG_NEIGHBOR_SYNC, FLAG_TEST_STUCK_BARRIER,
     DEV_NONFINITE, DEV_TIMEOUT, Plan, Problem, default_params, n_fields, n_params,
 )
 from ._lib import CGError  # noqa: F401

@@ -23,6 +23,7 @@ MIRROR, CLAMP = 0, 1
 EULER, HEUN, RK4 = 0, 1, 2
 FLAG_ALLOW_UNSTABLE = 1 << 0
 FLAG_PER_STAGE_LAUNCH = 1 << 1
+FLAG_NEIGHBOR_SYNC = 1 << 2
 FLAG_TEST_STUCK_BARRIER = 1 << 8
 DEV_NONFINITE, DEV_TIMEOUT = 1, 2
 ABI_VERSION = 1

@@ -9,8 +9,8 @@ knobs:
 * ``threads``, ``blocks_per_sm``: warps per SM of the persistent grid;
 * ``schedule``: static balanced segments, or the atomic tile queue with
   ``rows`` rows per tile;
-* synchronisation depth between stages: neighbour-only waits (default),
-  a grid-wide barrier, or one kernel launch per RK stage (the shallowest
+* synchronisation depth between stages: a grid-wide barrier (default),
+  neighbour-only waits, or one kernel launch per RK stage (the shallowest
   fusion: one stage per pass instead of every stage of the run in one pass).
 
 Every candidate computes each cell with the same arithmetic, so results are
@@ -27,14 +27,17 @@ import torch
 
 from . import api
 
-FLAG_GRID_BARRIER = 1 << 2
+FLAG_NEIGHBOR_SYNC = 1 << 2
 
 DEFAULT_CANDIDATES: List[Dict] = [
     dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0),
     dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=0),
     dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=0),
-    dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0, sync="grid"),
+    dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0, sync="neighbor"),
+    dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=0, sync="neighbor"),
     dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=1, rows=4),
+    dict(cells_x=1, threads=128, blocks_per_sm=4, schedule=1, rows=2),
+    dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=2),
     dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=1, rows=8),
     dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=4),
     dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0, sync="per_stage"),
@@ -61,8 +64,8 @@ def cache_key(problems) -> str:
 def _with_flags(problems, cand):
     out = []
     extra = 0
-    if cand.get("sync") == "grid":
-        extra = FLAG_GRID_BARRIER
+    if cand.get("sync") == "neighbor":
+        extra = FLAG_NEIGHBOR_SYNC
     elif cand.get("sync") == "per_stage":
         extra = api.FLAG_PER_STAGE_LAUNCH
     for p in problems:

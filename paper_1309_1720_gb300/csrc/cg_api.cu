@@ -124,6 +124,7 @@ struct cg_plan_s {
     std::vector<int2> deps;          // halo owners of each block (neighbour sync)
     int2 *d_deps = nullptr;
     int32_t sync_mode = cgk::SYNC_GRID;
+    double *d_tab = nullptr;         // 2^(j/32) table of the exponential
 };
 
 namespace {
@@ -247,14 +248,17 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         P.mp[38] = 1.0 / prm[8];        // 1/tvp
         P.mp[39] = 1.0 / prm[13];       // 1/twp
         P.mp[40] = 1.0 / prm[26];       // 1/twinf
-        P.mp[41] = -prm[11] * prm[12];  // -kwm uwm
-        P.mp[42] = -prm[19] * prm[20];  // -kso uso
-        P.mp[43] = -prm[23] * prm[24];  // -ks us
-        P.mp[44] = (prm[10] - prm[9]) / 2.0;    // (tw2m - tw1m) / 2
-        P.mp[45] = (prm[9] + prm[10]) / 2.0;    // (tw1m + tw2m) / 2
-        P.mp[46] = (prm[18] - prm[17]) / 2.0;   // (tso2 - tso1) / 2
-        P.mp[47] = (prm[17] + prm[18]) / 2.0;   // (tso1 + tso2) / 2
-        P.mp[48] = 6.0 * k;                     // 6 k
+        // (1 + tanh(a))/2 = sigmoid(2 a): the arguments are pre-doubled
+        P.mp[cgk::BD_AW2] = -2.0 * prm[11] * prm[12];
+        P.mp[cgk::BD_KW2] = 2.0 * prm[11];
+        P.mp[cgk::BD_ASO2] = -2.0 * prm[19] * prm[20];
+        P.mp[cgk::BD_KSO2] = 2.0 * prm[19];
+        P.mp[cgk::BD_AS2] = -2.0 * prm[23] * prm[24];
+        P.mp[cgk::BD_KS2] = 2.0 * prm[23];
+        P.mp[cgk::BD_DTW] = prm[10] - prm[9];
+        P.mp[cgk::BD_DTSO] = prm[18] - prm[17];
+        P.mp[cgk::BD_6K] = 6.0 * k;
+        static_assert(cgk::BD_N <= cgk::NMP, "model constant table too small");
         I.mi[0] = I.wc[0];
     }
 }
@@ -505,11 +509,18 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg);
         halo_dependencies(nxs, nys, P->nblocks, P->deps);
         P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
-                        !(P->flags & CG_FLAG_GRID_BARRIER)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
+                        (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
     }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_deps, sizeof(int2) * std::max<size_t>(1, P->deps.size()));
     if (e == cudaSuccess && !P->deps.empty())
         e = cudaMemcpy(P->d_deps, P->deps.data(), sizeof(int2) * P->deps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_tab, sizeof(double) * 32);
+    if (e == cudaSuccess) {
+        double tab[32];                       // 2^(j/32), rounded once from extended precision
+        for (int j = 0; j < 32; ++j) tab[j] = (double)std::exp2((long double)j / 32.0L);
+        e = cudaMemcpy(P->d_tab, tab, sizeof tab, cudaMemcpyHostToDevice);
+        for (Inst &I : P->inst) I.tab = P->d_tab;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_inst, sizeof(Inst) * n_inst);
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_inst, P->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
@@ -525,6 +536,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         if (P->d_segs) cudaFree(P->d_segs);
         if (P->d_warp_seg) cudaFree(P->d_warp_seg);
         if (P->d_deps) cudaFree(P->d_deps);
+        if (P->d_tab) cudaFree(P->d_tab);
         delete P;
         return cuda_fail(e, "plan creation");
     }
@@ -639,6 +651,7 @@ CG_API cg_status cg_plan_destroy(cg_plan plan)
     if (plan->d_segs) cudaFree(plan->d_segs);
     if (plan->d_warp_seg) cudaFree(plan->d_warp_seg);
     if (plan->d_deps) cudaFree(plan->d_deps);
+    if (plan->d_tab) cudaFree(plan->d_tab);
     delete plan;
     return CG_OK;
 }

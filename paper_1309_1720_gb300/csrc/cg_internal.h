@@ -24,6 +24,7 @@ struct Inst {
     int64_t ws_off;          // element offset of the instance's scratch block in the workspace
     double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights
     double mi[4];            // instance-dependent folds of centre weight and model constants
+    const double *tab;       // plan-owned table 2^(j/32), j = 0..31 (exponentials)
 };
 
 // A warp's share of one stage under the static schedule: columns

@@ -88,3 +88,47 @@ CG_API cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per
     if (seconds) *seconds = ms * 1e-3;
     return CG_OK;
 }
+
+// ------------------------------------------------ own elementary functions
+
+#include <cmath>
+
+#include "cg_fastmath.cuh"
+
+namespace {
+
+__global__ void k_check_fastmath(int fn, const double *x, double *own, double *ref, int64_t n, const double *tab)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        if (fn == 0) {
+            own[i] = cgk::fast_rcp(v);
+            ref[i] = 1.0 / v;
+        } else if (fn == 1) {
+            own[i] = cgk::exp_neg(v, tab);
+            ref[i] = exp(v);
+        } else {
+            double ds;
+            own[i] = cgk::sigmoid(v, tab, ds);
+            ref[i] = 0.5 * (1.0 + tanh(0.5 * v));
+        }
+    }
+}
+
+}  // namespace
+
+CG_API cg_status cg_check_fastmath(int32_t fn, const double *x, double *own, double *ref, int64_t n)
+{
+    if (fn < 0 || fn > 2 || !x || !own || !ref || n < 0) return CG_EINVAL;
+    double tab[32];
+    for (int j = 0; j < 32; ++j) tab[j] = (double)std::exp2((long double)j / 32.0L);
+    double *dtab = nullptr;
+    cudaError_t e = cudaMalloc(&dtab, sizeof tab);
+    if (e == cudaSuccess) e = cudaMemcpy(dtab, tab, sizeof tab, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_check_fastmath<<<1024, 256>>>(fn, x, own, ref, n, dtab);
+        e = cudaDeviceSynchronize();
+    }
+    if (dtab) cudaFree(dtab);
+    return e == cudaSuccess ? CG_OK : CG_ECUDA;
+}

@@ -21,6 +21,7 @@
 // assignment, no waiting).
 #pragma once
 
+#include "cg_fastmath.cuh"
 #include "cg_internal.h"
 
 namespace cgk {
@@ -254,13 +255,14 @@ enum {
     BD_IVP,            // 1/tvp
     BD_IWP,            // 1/twp
     BD_IWINF,          // 1/twinf
-    BD_AWM,            // -kwm uwm
-    BD_ASO,            // -kso uso
-    BD_AS,             // -ks us
-    BD_HDTW,           // (tw2m - tw1m) / 2
-    BD_MTW,            // (tw1m + tw2m) / 2
-    BD_HDSO,           // (tso2 - tso1) / 2
-    BD_MSO,            // (tso1 + tso2) / 2
+    BD_AW2,            // -2 kwm uwm
+    BD_KW2,            // 2 kwm
+    BD_ASO2,           // -2 kso uso
+    BD_KSO2,           // 2 kso
+    BD_AS2,            // -2 ks us
+    BD_KS2,            // 2 ks
+    BD_DTW,            // tw2m - tw1m
+    BD_DTSO,           // tso2 - tso1
     BD_6K,             // 6 k
     BD_N
 };
@@ -270,12 +272,12 @@ template <> struct Model<MODEL_BOCF> {
     // Stored Jacobian entries (wc_u folded into J_uu):
     // [J_uu, J_uv, J_uw, J_us, J_vu, J_vv, J_wu, J_ww, J_su, J_ss]
     static constexpr int NJ = 10;
-    struct Coef { double wc_u; };
-    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0]}; }
+    struct Coef { double wc_u; const double *tab; };
+    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.tab}; }
 
     // Shared body: right-hand side t and, when JAC, the Jacobian entries.
-    // Sigmoids (1 + tanh(a))/2 are written with tanh; time constants enter
-    // through their reciprocals.
+    // The three (1 + tanh(k (u - c)))/2 terms are sigmoids of 2 k (u - c)
+    // (cg_fastmath.cuh); time constants enter through fast reciprocals.
     template <bool JAC>
     __device__ __forceinline__ static void eval(const Coef &c, const double *mp, const double (&z)[NV],
                                                 double (&t)[NV], double *J)
@@ -286,23 +288,68 @@ template <> struct Model<MODEL_BOCF> {
         const double tw = clamp01_int(fma(k, u, mp[BD_CW]));
         const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
         const double to = clamp01_int(fma(k, u, mp[BD_CO]));
+        if constexpr (!JAC) {
+            // Warp-uniform shortcuts where the v and w switches are saturated
+            // for every lane.  Terms multiplied by an exact 0 are dropped and
+            // terms multiplied by an exact 1 kept, so the values equal the
+            // general path's.
+            const long long bv = __double_as_longlong(tv), bw = __double_as_longlong(tw);
+            const long long ONE = 0x3FF0000000000000ll;
+            if (__all_sync(CG_FULL, (bv | bw) == 0)) {
+                // resting tissue: H_v = H_w = 0 (only the u-dependent steady
+                // states and time constants near u = 0 remain)
+                const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);
+                const double Ho = (to * to) * fma(-2.0, to, 3.0);
+                const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
+                const double v_inf = 1.0 - Hvm;
+                const double sw = sigmoid(fma(mp[BD_KW2], u, mp[BD_AW2]), c.tab);
+                const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
+                const double q = fma(-u, mp[BD_IWINF], 1.0);
+                const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
+                const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
+                const double r_s = fast_rcp(mp[BP_TS1]);
+                const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab);
+                const double uo = u - mp[BP_UO];
+                t[0] = fma(c.wc_u, u, -(uo * r_o));
+                t[1] = (v_inf - v) * r_vm;
+                t[2] = (w_inf - w) * r_wm;
+                t[3] = (s_inf - s) * r_s;
+                return;
+            }
+            if (__all_sync(CG_FULL, bv == ONE && bw == ONE && __double_as_longlong(tvm) == ONE &&
+                                        __double_as_longlong(to) == ONE)) {
+                // excited tissue: every switch is 1
+                const double r_so = fast_rcp(fma(mp[BD_DTSO], sigmoid(fma(mp[BD_KSO2], u, mp[BD_ASO2]), c.tab),
+                                                 mp[BP_TSO1]));
+                const double r_s = fast_rcp(fma(1.0, mp[BD_DTS], mp[BP_TS1]));
+                const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab);
+                const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u;
+                const double J_fi = -v * (ua * ub) * mp[BD_IFI];
+                const double J_si = -w * (s * mp[BD_ISI]);
+                t[0] = fma(c.wc_u, u, -((J_fi + r_so) + J_si));
+                t[1] = -v * mp[BD_IVP];
+                t[2] = -w * mp[BD_IWP];
+                t[3] = (s_inf - s) * r_s;
+                return;
+            }
+        }
         const double Hv = (tv * tv) * fma(-2.0, tv, 3.0);
         const double Hw = (tw * tw) * fma(-2.0, tw, 3.0);
         const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);
         const double Ho = (to * to) * fma(-2.0, to, 3.0);
         const double tau_vm = fma(Hvm, mp[BD_DTV], mp[BP_TV1M]);
-        const double r_vm = 1.0 / tau_vm;
+        const double r_vm = fast_rcp(tau_vm);
         const double v_inf = 1.0 - Hvm;
-        const double th_w = tanh(fma(mp[BP_KWM], u, mp[BD_AWM]));
-        const double r_wm = 1.0 / fma(mp[BD_HDTW], th_w, mp[BD_MTW]);
+        double dsw, dsso, dss;
+        const double sw = sigmoid(fma(mp[BD_KW2], u, mp[BD_AW2]), c.tab, dsw);
+        const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
-        const double r_o = 1.0 / fma(Ho, mp[BD_DTO], mp[BP_TO1]);
-        const double th_so = tanh(fma(mp[BP_KSO], u, mp[BD_ASO]));
-        const double r_so = 1.0 / fma(mp[BD_HDSO], th_so, mp[BD_MSO]);
-        const double r_s = 1.0 / fma(Hw, mp[BD_DTS], mp[BP_TS1]);
-        const double th_s = tanh(fma(mp[BP_KS], u, mp[BD_AS]));
-        const double s_inf = fma(0.5, th_s, 0.5);
+        const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
+        const double sso = sigmoid(fma(mp[BD_KSO2], u, mp[BD_ASO2]), c.tab, dsso);
+        const double r_so = fast_rcp(fma(mp[BD_DTSO], sso, mp[BP_TSO1]));
+        const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
+        const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab, dss);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
         const double omHv = 1.0 - Hv, omHw = 1.0 - Hw;
         const double vinf_v = v_inf - v, winf_w = w_inf - w, sinf_s = s_inf - s;
@@ -320,12 +367,12 @@ template <> struct Model<MODEL_BOCF> {
             const double dHvm = k6 * (tvm * (1.0 - tvm));
             const double dHo = k6 * (to * (1.0 - to));
             const double dtau_vm = dHvm * mp[BD_DTV];
-            const double dtau_wm = mp[BD_HDTW] * mp[BP_KWM] * fma(-th_w, th_w, 1.0);
+            const double dtau_wm = mp[BD_DTW] * mp[BD_KW2] * dsw;
             const double dtau_o = dHo * mp[BD_DTO];
-            const double dtau_so = mp[BD_HDSO] * mp[BP_KSO] * fma(-th_so, th_so, 1.0);
+            const double dtau_so = mp[BD_DTSO] * mp[BD_KSO2] * dsso;
             const double dtau_s = dHw * mp[BD_DTS];
             const double dw_inf = fma(dHo, mp[BP_WINFSTAR] - q, -(1.0 - Ho) * mp[BD_IWINF]);
-            const double ds_inf = 0.5 * mp[BP_KS] * fma(-th_s, th_s, 1.0);
+            const double ds_inf = mp[BD_KS2] * dss;
             const double dJfi_du = -(v * mp[BD_IFI]) * fma(dHv, ua * ub, Hv * (ub - ua));
             const double dJfi_dv = -Hv * (ua * ub) * mp[BD_IFI];
             const double dJso_du = omHw * r_o - uo * dHw * r_o - uo * omHw * dtau_o * (r_o * r_o)

@@ -133,6 +133,30 @@ def test_gradient_fd_and_cpu_reference(cuda_ok):
     assert abs(float(dLdD[0]) - odLdD[0]) <= 1e-8 * abs(odLdD[0])
 
 
+@pytest.mark.parametrize("flags", [1 << 1, 1 << 2])
+def test_adjoint_and_tlm_other_sync_modes(cuda_ok, flags):
+    """Per-stage launches and neighbour synchronisation give the same
+    adjoint and tangents as the default grid barrier, bitwise."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, RK4, STENCIL9
+    p = _prob(0, 150, 97, STENCIL9, RK4)
+    z0 = torch.from_numpy(_z0(p)).cuda()
+    lamT = torch.from_numpy(I.unit_direction(z0.shape, 3)).cuda()
+    dz = lamT[None].contiguous()
+    a0, d0 = Plan(p).adjoint(z0, lamT, 21, checkpoint_every=4)
+    _, t0 = Plan(p).tlm(z0, dz, 21)
+    p.flags = flags
+    a1, d1 = Plan(p).adjoint(z0, lamT, 21, checkpoint_every=4)
+    _, t1 = Plan(p).tlm(z0, dz, 21)
+    assert torch.equal(a0, a1) and torch.equal(t0, t1)
+    if flags == 1 << 1:
+        # one launch per stage adds each stage's warp sums to the dL/dD slots
+        # instead of each launch's, a different association of the same terms
+        assert torch.allclose(d0, d1, rtol=1e-12, atol=0)
+    else:
+        assert torch.equal(d0, d1)
+
+
 def test_dLdD_bitwise_reproducible(cuda_ok):
     import torch
     from paper_1309_1720_gb300 import Plan, RK4, STENCIL9

@@ -48,11 +48,11 @@ def test_fhn_matrix(cuda_ok, stencil, scheme, bc, shape):
     dict(cells_x=1, rows=16, threads=256, blocks_per_sm=1, schedule=1), dict(cells_x=2, rows=64, threads=128, schedule=1),
     dict(cells_x=1, threads=256), dict(cells_x=2, threads=128, blocks_per_sm=2), dict(cells_x=1, threads=512),
 ])
-@pytest.mark.parametrize("per_stage", [False, True])
-def test_fhn_tunings_and_launch_modes(cuda_ok, tuning, per_stage):
-    from paper_1309_1720_gb300 import FLAG_PER_STAGE_LAUNCH, RK4, STENCIL9
-    p = _fhn(150, 97, stencil=STENCIL9, scheme=RK4, dt=2e-4,
-             flags=FLAG_PER_STAGE_LAUNCH if per_stage else 0)
+@pytest.mark.parametrize("mode", ["barrier", "per_stage", "neighbor"])
+def test_fhn_tunings_and_launch_modes(cuda_ok, tuning, mode):
+    from paper_1309_1720_gb300 import FLAG_PER_STAGE_LAUNCH, FLAG_NEIGHBOR_SYNC, RK4, STENCIL9
+    flags = {"barrier": 0, "per_stage": FLAG_PER_STAGE_LAUNCH, "neighbor": FLAG_NEIGHBOR_SYNC}[mode]
+    p = _fhn(150, 97, stencil=STENCIL9, scheme=RK4, dt=2e-4, flags=flags)
     z0 = I.fhn_broken_wave(150, 97, width=20)
     g = gpu_run(p, z0, 60, tuning=tuning)
     o = oracle_run(p, z0, 60)
