@@ -60,6 +60,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """Largest value of x over all ranks (the slowest replica's time)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cell_updates_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job GCUPS: every rank steps its own replica of the workload (the
+    path runs one instance per GPU; replicas share nothing), so the job's
+    cell-updates are ws times one rank's, over the slowest rank's time."""
+    return ws * cell_updates_per_rank / seconds / 1e9
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -214,21 +233,24 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         return min(ts)
 
     # 128^2 explicit Euler, 5-point, 1000 steps (launch/latency-bound size)
+    from paper_1309_1720_gb300 import autotune
     p = api.Problem(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
-    plan = plan_cls(p)
     z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
+    tun = autotune.tune([p], z, n_steps=200)
+    plan = autotune.tuned_plan([p], z, n_steps=200)
     t = timed(plan, z, 1000)
-    rows["fhn-128x128-5pt-euler-1000steps"] = {"gcups": 128 * 128 * 1000 / t / 1e9, "seconds": t}
+    rows["fhn-128x128-5pt-euler-1000steps"] = {"gcups": 128 * 128 * 1000 / t / 1e9, "seconds": t, "tuning": tun}
     plan.close()
 
     # 2048^2 four-field model, anisotropic 9-point, RK4 (500 of the 5000 steps)
     n, steps = 2048, 500
     p = api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
                     stencil=api.STENCIL9, scheme=api.RK4, dt=0.05)
-    plan = plan_cls(p)
     z = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
+    tun = autotune.tune([p], z, n_steps=10)
+    plan = autotune.tuned_plan([p], z, n_steps=10)
     t = timed(plan, z, steps, reps=2)
-    rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t,
+    rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "tuning": tun,
                                            "steps_timed": steps, "note": "rate of 500 of the 5000 steps"}
     plan.close()
 
@@ -239,8 +261,10 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     probs = [api.Problem(model=api.FHN, nx=int(n), ny=int(n), dx=0.04, D=(float(d), 1.5),
                          scheme=api.RK4, dt=2.5e-4) for n, d in zip(sizes, dus)]
     cells = int(np.sum(sizes.astype(np.int64) ** 2))
-    bp = plan_cls(probs)
-    zin = bp.pack(states)
+    from paper_1309_1720_gb300 import autotune
+    zin = plan_cls(probs).pack(states)
+    batch_tuning = autotune.tune(probs, zin, n_steps=20)
+    bp = autotune.tuned_plan(probs, zin, n_steps=20)
     zout = torch.empty_like(zin)
     bp.run(zin, steps, out=zout)
     torch.cuda.synchronize()
@@ -275,7 +299,9 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     rows["batch-256x(64..512)^2-5pt-rk4"] = {
         "gcups_batched": cells * steps / min(tb) / 1e9, "gcups_sequential": cells * steps / ts / 1e9,
         "speedup": ts / min(tb), "cells": cells, "steps_timed": steps, "bitwise_equal_to_sequential": same,
-        "note": "rate of 200 of the 2000 steps; batched = one graph-replayed persistent launch"}
+        "tuning": batch_tuning,
+        "note": "rate of 200 of the 2000 steps; batched = one graph-replayed persistent launch, launch shape "
+                "from the autotuner"}
     for sp in seq_plans:
         sp.close()
     bp.close()
@@ -345,7 +371,9 @@ def main():
     z0 = torch.from_numpy(z0_host).cuda()
     tuning = None
     if args.profile_case:
-        plan = Plan(prob)
+        # the launch shape the bench itself chose, if it ran before on this machine
+        from paper_1309_1720_gb300 import autotune
+        plan = autotune.plan_for([prob], autotune.cached([prob]))
     else:
         # launch shape chosen by the project's autotuner on a short run of the
         # same workload (cached per GPU / model / size class)
@@ -359,8 +387,9 @@ def main():
         if args.profile_case == "bocf":
             # four-field 2048^2 anisotropic 9-point RK4: 640 MB working set
             n = 2048
-            plan = Plan(api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
-                                    stencil=api.STENCIL9, scheme=api.RK4, dt=0.05))
+            bp = api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
+                             stencil=api.STENCIL9, scheme=api.RK4, dt=0.05)
+            plan = autotune.plan_for([bp], autotune.cached([bp]))
             z0 = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
             out = torch.empty_like(z0)
             steps = 2
@@ -404,12 +433,8 @@ def main():
         t_wall = time.perf_counter() - t_wall
     plan.status()
     secs = [a.elapsed_time(b) / 1e3 for a, b in times]
-    tot = sum(secs)
-    if ws > 1:
-        tt = torch.tensor([tot], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tot = float(tt.item())
-    value = ws * cells * args.steps / tot / 1e9
+    tot = max_over_ranks(sum(secs), ws)
+    value = replica_throughput(cells * args.steps, ws, tot)
     launch_s = statistics.median(secs)
     achieved_tflops = FLOPS_PER_CELL_UPDATE * cells / launch_s / 1e12
 
@@ -430,11 +455,7 @@ def main():
         e1.record(stream)
         e2e_t.append((e0, e1))
     barrier()
-    e2e_tot = sum(a.elapsed_time(b) / 1e3 for a, b in e2e_t)
-    if ws > 1:
-        tt = torch.tensor([e2e_tot], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(tt.item())
+    e2e_tot = max_over_ranks(sum(a.elapsed_time(b) / 1e3 for a, b in e2e_t), ws)
     nbytes = z0.numel() * 8
 
     rows = None

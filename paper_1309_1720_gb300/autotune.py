@@ -140,6 +140,25 @@ def tune(problems, z_in: torch.Tensor, n_steps: int = 50, candidates: Optional[L
     return best
 
 
+def cached(problems) -> Optional[Dict]:
+    """The cached winner for these problems, or None (no timing runs)."""
+    if isinstance(problems, api.Problem):
+        problems = [problems]
+    try:
+        return json.load(open(cache_path()))[cache_key(problems)]["best"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def plan_for(problems, cand: Optional[Dict]) -> api.Plan:
+    """Plan with a given candidate (None: library defaults)."""
+    if isinstance(problems, api.Problem):
+        problems = [problems]
+    if cand is None:
+        return api.Plan(problems)
+    return api.Plan(_with_flags(problems, cand), tuning=_tuning(cand))
+
+
 def tuned_plan(problems, z_in: torch.Tensor, **kw) -> api.Plan:
     """Plan built with the tuned launch shape."""
     if isinstance(problems, api.Problem):
