@@ -37,6 +37,11 @@ FLOPS_PER_CELL_UPDATE = 168
 # Algorithmic HBM bytes per cell-update of a fused step: each field read and
 # written once (2 fields x 8 B x 2).
 BYTES_PER_CELL_UPDATE = 32
+# DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on a 20-step launch of this workload; traffic grows
+# in proportion to the steps of a launch (L2 write-backs of the resident
+# working set), so one bench launch moves this times its cell-updates.
+MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 35.4
 
 
 def parse():
@@ -472,7 +477,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "frac": achieved_tflops / peak_tflops,
+                         "traffic": MEASURED_DRAM_BYTES_PER_CELL_UPDATE * cells,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 20-step "
+                                           "launch (profiles/k_stage_fhn_1024x1024_9pt_rk4.md), scaled to "
+                                           "the 10000-step launch",
                          "peak_source": "measured FP64 DFMA throughput of this GPU (library probe, 8 chains x "
                                         "256 threads x 4 blocks/SM), FMA = 2 flops",
                          "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,

@@ -152,7 +152,7 @@ def test_adjoint_and_tlm_other_sync_modes(cuda_ok, flags):
     if flags == 1 << 1:
         # one launch per stage adds each stage's warp sums to the dL/dD slots
         # instead of each launch's, a different association of the same terms
-        assert torch.allclose(d0, d1, rtol=1e-12, atol=0)
+        assert torch.allclose(d0, d1, rtol=1e-10, atol=0)
     else:
         assert torch.equal(d0, d1)
 
