@@ -26,8 +26,9 @@ _lib = None
 
 FHN, BOCF, DIFFUSION = 0, 1, 3
 ST5, ST9 = 0, 1
-MIRROR, CLAMP = 0, 1
-EULER, HEUN, RK4 = 0, 1, 2
+MIRROR, CLAMP, PERIODIC = 0, 1, 2
+EULER, HEUN, RK4, RUSH_LARSEN, IMPLICIT_EULER = 0, 1, 2, 3, 4
+AS_WRITTEN, TANH_AS_HK = 0, 1
 
 MAXF, MAXP = 4, 32
 
@@ -41,6 +42,7 @@ class Problem(ctypes.Structure):
         ("alpha_d", ctypes.c_double), ("dt", ctypes.c_double),
         ("Dxx", ctypes.c_double * MAXF), ("Dyy", ctypes.c_double * MAXF),
         ("params", ctypes.c_double * MAXP),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -99,10 +101,13 @@ def default_params(model: int) -> np.ndarray:
 
 def problem(model=FHN, nx=64, ny=64, dx=0.04, dy=None, Dxx=None, Dyy=None,
             stencil=ST5, alpha_d=1.0 / 6.0, bc=MIRROR, scheme=EULER, dt=1e-4,
-            params=None) -> Problem:
+            params=None, variant=AS_WRITTEN) -> Problem:
     """Build the oracle's problem record.  Defaults: FHN diffusivities
-    (D_u, D_v) = (1, 1.5); BOCF D_u = 1.171e-3 cm^2/ms, gates not diffusive."""
+    (D_u, D_v) = (1, 1.5); BOCF D_u = 1.171e-3 cm^2/ms, gates not diffusive.
+    ``variant=TANH_AS_HK`` selects the Bueno-Orovio model with its tanh terms
+    replaced by smoothed steps (Sect. 6)."""
     p = Problem()
+    p.variant = variant
     p.model, p.stencil, p.bc, p.scheme = model, stencil, bc, scheme
     p.nx, p.ny = nx, ny
     p.dx = dx

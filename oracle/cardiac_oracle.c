@@ -17,6 +17,9 @@
  *   FitzHugh-Nagumo                                             Eq. (fhn)
  *   Bueno-Orovio-Cherry-Fenton with cubic smoothed steps H_k    Eq. (bochfe), Sect. 2
  *   explicit Euler, Heun, classic RK4, fixed dt                 Sect. 3
+ *   Rush-Larsen and implicit Euler on the Bueno-Orovio gates    Sect. 3, Table 2
+ *   periodic ghosts (opposite-edge values)                      Sect. 3
+ *   tanh replaced by 2 H_k - 1 (opt-in model variant)           Sect. 6
  * plus the tangent-linear and discrete adjoint of one explicit RK step (the
  * exact Jacobian of the discrete flow that the Newton-Krylov motivation of
  * Sect. 1 needs).
@@ -29,7 +32,12 @@
  *  - MIRROR ghost: index -1 maps to 1 and n to n-2 (CLAMP: -1 -> 0, n -> n-1);
  *  - the s-gate of Eq. (bochfe) divides by tau_s;
  *  - the u-dependent time constants and steady states of the cited
- *    Bueno-Orovio model, with every step function replaced by H_k.
+ *    Bueno-Orovio model, with every step function replaced by H_k;
+ *  - Rush-Larsen / implicit Euler: u takes an explicit Euler step, the gates
+ *    v, w, s (linear in themselves) are advanced with u frozen at the start
+ *    of the step;
+ *  - the tanh variant replaces (1 + tanh(kk x))/2 by H_{kk/3}(x), the smooth
+ *    step with the same value and slope at x = 0.
  * Model constants of the Bueno-Orovio epicardial set are not printed in the
  * paper: parity unpinned for those values.
  */
@@ -39,8 +47,9 @@
 
 enum { ORC_FHN = 0, ORC_BOCF = 1, ORC_DIFFUSION = 3 };
 enum { ORC_ST5 = 0, ORC_ST9 = 1 };
-enum { ORC_MIRROR = 0, ORC_CLAMP = 1 };
-enum { ORC_EULER = 0, ORC_HEUN = 1, ORC_RK4 = 2 };
+enum { ORC_MIRROR = 0, ORC_CLAMP = 1, ORC_PERIODIC = 2 };
+enum { ORC_EULER = 0, ORC_HEUN = 1, ORC_RK4 = 2, ORC_RUSH_LARSEN = 3, ORC_IMPLICIT_EULER = 4 };
+enum { ORC_AS_WRITTEN = 0, ORC_TANH_AS_HK = 1 };
 
 #define ORC_MAXF 4
 #define ORC_MAXP 32
@@ -51,6 +60,7 @@ typedef struct {
     double dx, dy, alpha_d, dt;
     double Dxx[ORC_MAXF], Dyy[ORC_MAXF];
     double params[ORC_MAXP];
+    int variant;        /* ORC_AS_WRITTEN or ORC_TANH_AS_HK (Bueno-Orovio only) */
 } orc_problem;
 
 /* ------------------------------------------------------------------ models */
@@ -131,6 +141,58 @@ double orc_dHk(double x, double k)
     return 6.0 * k * t * (1.0 - t);
 }
 
+/* (1 + tanh(kk (u - cc)))/2 of the cited model, or H_{kk/3}(u - cc) under
+ * the tanh variant of Sect. 6 (same value 1/2 and slope kk/2 at u = cc);
+ * *d receives the derivative with respect to u. */
+static double half_tanh(const orc_problem *p, double u, double kk, double cc, double *d)
+{
+    if (p->variant == ORC_TANH_AS_HK) {
+        *d = orc_dHk(u - cc, kk / 3.0);
+        return orc_Hk(u - cc, kk / 3.0);
+    }
+    double th = tanh(kk * (u - cc));
+    *d = kk * (1.0 - th * th) / 2.0;
+    return (1.0 + th) / 2.0;
+}
+
+/* Eq. (bochfe) with the currents and the alpha/beta gate form: f = N[z] at
+ * one cell and, when alpha is not NULL, the coefficients of the gate
+ * equations dx/dt = alpha_x(u) x + beta_x(u) for x = v, w, s. */
+static void bocf_eval(const orc_problem *p, const double *z, double *f, double *alpha, double *beta)
+{
+    const double *q = p->params;
+    double d;
+    double u = z[0], v = z[1], w = z[2], s = z[3];
+    double k = q[B_K];
+    /* u-dependent quantities of the cited model */
+    double tau_vm = (1.0 - orc_Hk(u - q[B_THVM], k)) * q[B_TV1M] + orc_Hk(u - q[B_THVM], k) * q[B_TV2M];
+    double v_inf = orc_Hk(q[B_THVM] - u, k);
+    double tau_wm = q[B_TW1M] + (q[B_TW2M] - q[B_TW1M]) * half_tanh(p, u, q[B_KWM], q[B_UWM], &d);
+    double w_inf = (1.0 - orc_Hk(u - q[B_THO], k)) * (1.0 - u / q[B_TWINF]) + orc_Hk(u - q[B_THO], k) * q[B_WINFSTAR];
+    double tau_o = (1.0 - orc_Hk(u - q[B_THO], k)) * q[B_TO1] + orc_Hk(u - q[B_THO], k) * q[B_TO2];
+    double tau_so = q[B_TSO1] + (q[B_TSO2] - q[B_TSO1]) * half_tanh(p, u, q[B_KSO], q[B_USO], &d);
+    double tau_s = (1.0 - orc_Hk(u - q[B_THW], k)) * q[B_TS1] + orc_Hk(u - q[B_THW], k) * q[B_TS2];
+    double s_inf = half_tanh(p, u, q[B_KS], q[B_US], &d);
+    /* currents */
+    double J_fi = -v * orc_Hk(u - q[B_THV], k) * (u - q[B_THV]) * (q[B_UU] - u) / q[B_TFI];
+    double J_so = (u - q[B_UO]) * orc_Hk(q[B_THW] - u, k) / tau_o + orc_Hk(u - q[B_THW], k) / tau_so;
+    double J_si = -orc_Hk(u - q[B_THW], k) * w * s / q[B_TSI];
+    /* gates: d x/dt = alpha_x(u) x + beta_x(u) */
+    double alpha_v = -orc_Hk(u - q[B_THV], k) / q[B_TVP] - orc_Hk(q[B_THV] - u, k) / tau_vm;
+    double beta_v = orc_Hk(q[B_THV] - u, k) * v_inf / tau_vm;
+    double alpha_w = -orc_Hk(u - q[B_THW], k) / q[B_TWP] - orc_Hk(q[B_THW] - u, k) / tau_wm;
+    double beta_w = orc_Hk(q[B_THW] - u, k) * w_inf / tau_wm;
+    f[0] = -(J_fi + J_so + J_si);
+    f[1] = alpha_v * v + beta_v;
+    f[2] = alpha_w * w + beta_w;
+    f[3] = (s_inf - s) / tau_s;
+    if (alpha) {
+        alpha[0] = alpha_v; beta[0] = beta_v;
+        alpha[1] = alpha_w; beta[1] = beta_w;
+        alpha[2] = -1.0 / tau_s; beta[2] = s_inf / tau_s;
+    }
+}
+
 /* N[z] at one cell.  z and f hold the n_v fields of that cell. */
 void orc_pointwise(const orc_problem *p, const double *z, double *f)
 {
@@ -146,30 +208,7 @@ void orc_pointwise(const orc_problem *p, const double *z, double *f)
         f[0] = 0.0;
         return;
     }
-    /* Eq. (bochfe) with the currents and the alpha/beta gate form. */
-    double u = z[0], v = z[1], w = z[2], s = z[3];
-    double k = q[B_K];
-    /* u-dependent quantities of the cited model */
-    double tau_vm = (1.0 - orc_Hk(u - q[B_THVM], k)) * q[B_TV1M] + orc_Hk(u - q[B_THVM], k) * q[B_TV2M];
-    double v_inf = orc_Hk(q[B_THVM] - u, k);
-    double tau_wm = q[B_TW1M] + (q[B_TW2M] - q[B_TW1M]) * (1.0 + tanh(q[B_KWM] * (u - q[B_UWM]))) / 2.0;
-    double w_inf = (1.0 - orc_Hk(u - q[B_THO], k)) * (1.0 - u / q[B_TWINF]) + orc_Hk(u - q[B_THO], k) * q[B_WINFSTAR];
-    double tau_o = (1.0 - orc_Hk(u - q[B_THO], k)) * q[B_TO1] + orc_Hk(u - q[B_THO], k) * q[B_TO2];
-    double tau_so = q[B_TSO1] + (q[B_TSO2] - q[B_TSO1]) * (1.0 + tanh(q[B_KSO] * (u - q[B_USO]))) / 2.0;
-    double tau_s = (1.0 - orc_Hk(u - q[B_THW], k)) * q[B_TS1] + orc_Hk(u - q[B_THW], k) * q[B_TS2];
-    /* currents */
-    double J_fi = -v * orc_Hk(u - q[B_THV], k) * (u - q[B_THV]) * (q[B_UU] - u) / q[B_TFI];
-    double J_so = (u - q[B_UO]) * orc_Hk(q[B_THW] - u, k) / tau_o + orc_Hk(u - q[B_THW], k) / tau_so;
-    double J_si = -orc_Hk(u - q[B_THW], k) * w * s / q[B_TSI];
-    /* gates: d x/dt = alpha_x(u) x + beta_x(u) */
-    double alpha_v = -orc_Hk(u - q[B_THV], k) / q[B_TVP] - orc_Hk(q[B_THV] - u, k) / tau_vm;
-    double beta_v = orc_Hk(q[B_THV] - u, k) * v_inf / tau_vm;
-    double alpha_w = -orc_Hk(u - q[B_THW], k) / q[B_TWP] - orc_Hk(q[B_THW] - u, k) / tau_wm;
-    double beta_w = orc_Hk(q[B_THW] - u, k) * w_inf / tau_wm;
-    f[0] = -(J_fi + J_so + J_si);
-    f[1] = alpha_v * v + beta_v;
-    f[2] = alpha_w * w + beta_w;
-    f[3] = ((1.0 + tanh(q[B_KS] * (u - q[B_US]))) / 2.0 - s) / tau_s;
+    bocf_eval(p, z, f, NULL, NULL);
 }
 
 /* Jacobian dN/dz at one cell, row-major J[i*n_v + j] = dN_i/dz_j, derived by
@@ -198,9 +237,9 @@ void orc_pointwise_jac(const orc_problem *p, const double *z, double *J)
     double dtau_vm = dH3 * (q[B_TV2M] - q[B_TV1M]);
     double v_inf = 1.0 - H3, dv_inf = -dH3;
 
-    double th_w = tanh(q[B_KWM] * (u - q[B_UWM]));
-    double tau_wm = q[B_TW1M] + (q[B_TW2M] - q[B_TW1M]) * (1.0 + th_w) / 2.0;
-    double dtau_wm = (q[B_TW2M] - q[B_TW1M]) * q[B_KWM] * (1.0 - th_w * th_w) / 2.0;
+    double dsw, sw = half_tanh(p, u, q[B_KWM], q[B_UWM], &dsw);
+    double tau_wm = q[B_TW1M] + (q[B_TW2M] - q[B_TW1M]) * sw;
+    double dtau_wm = (q[B_TW2M] - q[B_TW1M]) * dsw;
 
     double w_inf = (1.0 - H4) * (1.0 - u / q[B_TWINF]) + H4 * q[B_WINFSTAR];
     double dw_inf = -dH4 * (1.0 - u / q[B_TWINF]) - (1.0 - H4) / q[B_TWINF] + dH4 * q[B_WINFSTAR];
@@ -208,14 +247,13 @@ void orc_pointwise_jac(const orc_problem *p, const double *z, double *J)
     double tau_o = (1.0 - H4) * q[B_TO1] + H4 * q[B_TO2];
     double dtau_o = dH4 * (q[B_TO2] - q[B_TO1]);
 
-    double th_so = tanh(q[B_KSO] * (u - q[B_USO]));
-    double tau_so = q[B_TSO1] + (q[B_TSO2] - q[B_TSO1]) * (1.0 + th_so) / 2.0;
-    double dtau_so = (q[B_TSO2] - q[B_TSO1]) * q[B_KSO] * (1.0 - th_so * th_so) / 2.0;
+    double dsso, sso = half_tanh(p, u, q[B_KSO], q[B_USO], &dsso);
+    double tau_so = q[B_TSO1] + (q[B_TSO2] - q[B_TSO1]) * sso;
+    double dtau_so = (q[B_TSO2] - q[B_TSO1]) * dsso;
 
     double tau_s = (1.0 - H2) * q[B_TS1] + H2 * q[B_TS2];
     double dtau_s = dH2 * (q[B_TS2] - q[B_TS1]);
-    double th_s = tanh(q[B_KS] * (u - q[B_US]));
-    double s_inf = (1.0 + th_s) / 2.0, ds_inf = q[B_KS] * (1.0 - th_s * th_s) / 2.0;
+    double ds_inf, s_inf = half_tanh(p, u, q[B_KS], q[B_US], &ds_inf);
 
     /* J_fi = -v H1 (u - thv)(uu - u) / tfi */
     double a = (u - q[B_THV]), b = (q[B_UU] - u);
@@ -256,8 +294,12 @@ void orc_pointwise_jac(const orc_problem *p, const double *z, double *J)
 
 /* ------------------------------------------------------------- diffusion */
 
+/* Neighbour index with the ghost rule of Sect. 3: MIRROR flips the
+ * displacement back into the grid, CLAMP repeats the edge value, PERIODIC
+ * takes the opposite edge's value. */
 static long map_index(long i, long n, int bc)
 {
+    if (bc == ORC_PERIODIC) return ((i % n) + n) % n;
     if (i < 0) return bc == ORC_MIRROR ? -i : 0;
     if (i >= n) return bc == ORC_MIRROR ? 2 * (n - 1) - i : n - 1;
     return i;
@@ -361,6 +403,31 @@ static void step_once(const orc_problem *p, double *z, long m,
         for (long i = 0; i < m; ++i) y[i] = z[i] + dt * k1[i];
         orc_rhs(p, y, k2);
         for (long i = 0; i < m; ++i) z[i] = z[i] + dt / 2.0 * (k1[i] + k2[i]);
+    } else if (p->scheme == ORC_RUSH_LARSEN || p->scheme == ORC_IMPLICIT_EULER) {
+        /* Sect. 3 / Table 2: u takes an explicit Euler step; each gate
+         * x = v, w, s obeys dx/dt = alpha x + beta with alpha, beta taken at
+         * the step's starting state.  Rush-Larsen integrates that linear
+         * equation exactly, x_inf + (x - x_inf) exp(alpha dt) with
+         * x_inf = -beta/alpha; implicit Euler solves
+         * x' = x + dt (alpha x' + beta) for x'. */
+        long n = p->nx * p->ny;
+        double zc[ORC_MAXF], fc[ORC_MAXF], al[3], be[3];
+        orc_rhs(p, z, k1);
+        for (long i = 0; i < n; ++i) {
+            for (int c = 0; c < 4; ++c) zc[c] = z[c * n + i];
+            bocf_eval(p, zc, fc, al, be);
+            z[i] = z[i] + dt * k1[i];
+            for (int g = 0; g < 3; ++g) {
+                double x = zc[g + 1], x1;
+                if (p->scheme == ORC_RUSH_LARSEN) {
+                    double x_inf = -be[g] / al[g];
+                    x1 = x_inf + (x - x_inf) * exp(al[g] * dt);
+                } else {
+                    x1 = (x + dt * be[g]) / (1.0 - dt * al[g]);
+                }
+                z[(g + 1) * n + i] = x1;
+            }
+        }
     } else {
         orc_rhs(p, z, k1);
         for (long i = 0; i < m; ++i) y[i] = z[i] + dt / 2.0 * k1[i];
@@ -379,6 +446,7 @@ int orc_step(const orc_problem *p, double *z, long n_steps)
 {
     int nv = orc_n_fields(p->model);
     if (nv < 0 || p->nx < 2 || p->ny < 2) return -1;
+    if ((p->scheme == ORC_RUSH_LARSEN || p->scheme == ORC_IMPLICIT_EULER) && p->model != ORC_BOCF) return -3;
     long m = nv * p->nx * p->ny;
     double *buf = malloc(sizeof(double) * (size_t)(5 * m));
     if (!buf) return -2;
@@ -398,6 +466,7 @@ static int tableau(int scheme, double A[4][4], double b[4])
     memset(b, 0, sizeof(double) * 4);
     if (scheme == ORC_EULER) { b[0] = 1.0; return 1; }
     if (scheme == ORC_HEUN) { A[1][0] = 1.0; b[0] = 0.5; b[1] = 0.5; return 2; }
+    if (scheme != ORC_RK4) return -1;   /* the gate integrators have no tableau */
     A[1][0] = 0.5; A[2][1] = 0.5; A[3][2] = 1.0;
     b[0] = 1.0 / 6.0; b[1] = 1.0 / 3.0; b[2] = 1.0 / 3.0; b[3] = 1.0 / 6.0;
     return 4;
@@ -455,6 +524,7 @@ int orc_tlm(const orc_problem *p, double *z, double *dz, long n_steps)
     long n = p->nx * p->ny, m = nv * n;
     double A[4][4], b[4];
     int ns = tableau(p->scheme, A, b);
+    if (ns < 0) return -3;
     double dt = p->dt;
     double *K = malloc(sizeof(double) * (size_t)(4 * m));
     double *dK = malloc(sizeof(double) * (size_t)(4 * m));
@@ -498,6 +568,7 @@ int orc_adjoint(const orc_problem *p, const double *z0, const double *lamT,
     long n = p->nx * p->ny, m = nv * n;
     double A[4][4], b[4];
     int ns = tableau(p->scheme, A, b);
+    if (ns < 0) return -3;
     double dt = p->dt;
     double *Z = malloc(sizeof(double) * (size_t)(m * (n_steps + 1)));
     double *Ys = malloc(sizeof(double) * (size_t)(4 * m));
