@@ -61,10 +61,19 @@ enum { CG_FHN = 0, CG_BOCF = 1, CG_KARMA = 2, CG_DIFFUSION = 3 };
 /* Laplacian (Eq. diffusion): 5-point, or 9-point with diagonal weight alpha_d. */
 enum { CG_STENCIL5 = 0, CG_STENCIL9 = 1 };
 /* Ghost points (Fig. 1): MIRROR maps index -1 to 1 and n to n-2 (the
- * displacement is flipped back into the grid); CLAMP maps -1 to 0, n to n-1. */
-enum { CG_BC_MIRROR = 0, CG_BC_CLAMP = 1 };
-/* Explicit integrators of Sect. 3. */
-enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2 };
+ * displacement is flipped back into the grid); CLAMP maps -1 to 0, n to n-1;
+ * PERIODIC maps -1 to n-1 and n to 0 (opposite-edge values, Sect. 3).  Under
+ * PERIODIC, CG_FLAG_NEIGHBOR_SYNC is ignored (the grid barrier is used). */
+enum { CG_BC_MIRROR = 0, CG_BC_CLAMP = 1, CG_BC_PERIODIC = 2 };
+/* Integrators of Sect. 3.  EULER, HEUN and RK4 are explicit for every field.
+ * RUSH_LARSEN and IMPLICIT_EULER (Table 2) apply to the four-field model
+ * only: u takes an explicit Euler step and each gate x = v, w, s, whose
+ * equation is linear in x (dx/dt = al(u) x + be(u)), is advanced with al, be
+ * taken at the step's starting state, by x_inf + (x - x_inf) e^(al dt) with
+ * x_inf = -be/al (Rush-Larsen) or by (x + dt be)/(1 - dt al) (implicit
+ * Euler).  They need positive time constants; the tangent-linear, adjoint
+ * and Newton entry points return CG_EUNSUPPORTED for them. */
+enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2, CG_RUSH_LARSEN = 3, CG_IMPLICIT_EULER = 4 };
 
 /* cg_problem.flags */
 #define CG_FLAG_ALLOW_UNSTABLE   (1u << 0)  /* skip the dt stability check */
@@ -72,8 +81,11 @@ enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2 };
                                                persistent cooperative launch per run */
 #define CG_FLAG_NEIGHBOR_SYNC    (1u << 2)  /* static schedule only: between stages each block
                                                waits for the blocks that own its halo instead of
-                                               a grid-wide barrier (measured slower on GB300 for
-                                               the configurations here; an autotuner option) */
+                                               a grid-wide barrier (an autotuner option) */
+#define CG_FLAG_TANH_AS_HK       (1u << 3)  /* four-field model only: the model variant of
+                                               Sect. 6, each (1 + tanh(kk x))/2 replaced by the
+                                               smoothed step H_{kk/3}(x) (same value and slope at
+                                               x = 0).  Changes the model, not only its cost. */
 #define CG_FLAG_TEST_STUCK_BARRIER (1u << 8) /* testing only: the first wait between stages
                                                expects one arrival (or one stage) more than can
                                                happen, so it must give up after
@@ -91,8 +103,8 @@ typedef struct cg_problem {
     double Dxx[4], Dyy[4]; /* per-field diagonal diffusion tensor; 0 = field not diffusive.
                               FHN: (1, delta = 1.5); BOCF: (1.171e-3 cm^2/ms, 0, 0, 0) */
     int32_t stencil;       /* CG_STENCIL5 / CG_STENCIL9 */
-    int32_t bc;            /* CG_BC_MIRROR / CG_BC_CLAMP */
-    int32_t scheme;        /* CG_EULER / CG_HEUN / CG_RK4 */
+    int32_t bc;            /* CG_BC_MIRROR / CG_BC_CLAMP / CG_BC_PERIODIC */
+    int32_t scheme;        /* CG_EULER / CG_HEUN / CG_RK4 / CG_RUSH_LARSEN / CG_IMPLICIT_EULER */
     uint32_t flags;        /* CG_FLAG_* */
     double alpha_d;        /* 9-point diagonal weight (axial weight 1 - 2 alpha_d); ignored for 5-point */
     double dt;             /* fixed time step */
@@ -121,8 +133,10 @@ typedef struct cg_plan_s *cg_plan;
 /* ---------------------------------------------------------------- plans */
 
 /* Validate a problem and build an immutable plan (coefficients, tile table,
- * launch shape).  Returns CG_EINVAL for a bad argument and CG_EUNSTABLE when
- * dt exceeds the linear bound 2/rho (Euler, Heun) or 2.785/rho (RK4), rho
+ * launch shape).  Returns CG_EINVAL for a bad argument, CG_EUNSUPPORTED for a
+ * gate integrator or CG_FLAG_TANH_AS_HK with a model other than CG_BOCF, and
+ * CG_EUNSTABLE when dt exceeds the linear bound 2/rho (Euler, Heun and the
+ * u step of the gate integrators) or 2.785/rho (RK4), rho
  * the spectral radius of the diffusion operator, unless
  * CG_FLAG_ALLOW_UNSTABLE is set.  Allocates a small device table on the
  * current device; *out is NULL on error. */

@@ -19,11 +19,12 @@ from ._lib import CProblem, CTuning, check
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENAN, ETIMEOUT, EUNSUPPORTED = range(8)
 FHN, BOCF, KARMA, DIFFUSION = 0, 1, 2, 3
 STENCIL5, STENCIL9 = 0, 1
-MIRROR, CLAMP = 0, 1
-EULER, HEUN, RK4 = 0, 1, 2
+MIRROR, CLAMP, PERIODIC = 0, 1, 2
+EULER, HEUN, RK4, RUSH_LARSEN, IMPLICIT_EULER = 0, 1, 2, 3, 4
 FLAG_ALLOW_UNSTABLE = 1 << 0
 FLAG_PER_STAGE_LAUNCH = 1 << 1
 FLAG_NEIGHBOR_SYNC = 1 << 2
+FLAG_TANH_AS_HK = 1 << 3
 FLAG_TEST_STUCK_BARRIER = 1 << 8
 DEV_NONFINITE, DEV_TIMEOUT = 1, 2
 ABI_VERSION = 1

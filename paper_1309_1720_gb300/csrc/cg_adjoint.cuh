@@ -14,7 +14,8 @@
 // L^T k = W L (W^-1 k).  The kernel doubles every loaded value that lies on
 // a boundary row or column, applies the forward stencil, and halves the
 // off-centre sum of boundary cells; all factors are powers of two, hence
-// exact.  Under CLAMP ghosts L is symmetric and no scaling is applied.
+// exact.  Under CLAMP and PERIODIC ghosts L is symmetric and no scaling is
+// applied.
 //
 // dL/dD partial sums live in one slot per warp of the static schedule and
 // are summed in a fixed order at the end, so gradients are bitwise

@@ -72,7 +72,21 @@ int n_params(int model)
 
 int n_stages(int scheme)
 {
-    return scheme == CG_EULER ? 1 : scheme == CG_HEUN ? 2 : 4;
+    return scheme == CG_HEUN ? 2 : scheme == CG_RK4 ? 4 : 1;
+}
+
+// Rush-Larsen / implicit Euler on the gates (no Butcher tableau, no
+// tangent-linear or adjoint kernels).
+bool gate_scheme(int scheme)
+{
+    return scheme == CG_RUSH_LARSEN || scheme == CG_IMPLICIT_EULER;
+}
+
+// Kernel family of a problem: the model, or the tanh-as-smoothed-step
+// variant of the four-field model.
+int kernel_model(int model, uint32_t flags)
+{
+    return (model == CG_BOCF && (flags & CG_FLAG_TANH_AS_HK)) ? cgk::MODEL_BOCFH : model;
 }
 
 // Default constants.  FHN: (eps, a1, a0) of Sect. 2.  BOCF: epicardial set
@@ -99,6 +113,7 @@ bool finite(double x) { return std::isfinite(x); }
 
 struct cg_plan_s {
     int32_t model = 0, stencil = 0, bc = 0, scheme = 0, nv = 0, ns = 0;
+    int32_t kmodel = 0;              // kernel family (kernel_model)
     uint32_t flags = 0;
     double dt = 0;
     int device = 0;
@@ -129,12 +144,13 @@ struct cg_plan_s {
 
 namespace {
 
-const void *lookup_kernel(int model, int stencil, int scheme, int cx)
+const void *lookup_kernel(int kmodel, int stencil, int scheme, int cx)
 {
-    switch (model) {
+    switch (kmodel) {
     case CG_FHN: return cgk::fwd_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::fwd_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::fwd_kernel_diff(stencil, scheme, cx);
+    case cgk::MODEL_BOCFH: return cgk::fwd_kernel_bocfh(stencil, scheme, cx);
     default: return nullptr;
     }
 }
@@ -186,10 +202,24 @@ cg_status validate(const cg_problem *p, int idx)
         return fail(CG_EINVAL, "problem %d: unknown stencil %d", idx, p->stencil);
     if (p->stencil == CG_STENCIL9 && (!finite(p->alpha_d) || p->alpha_d < 0 || p->alpha_d > 0.25))
         return fail(CG_EINVAL, "problem %d: alpha_d %g outside [0, 1/4]", idx, p->alpha_d);
-    if (p->bc != CG_BC_MIRROR && p->bc != CG_BC_CLAMP)
+    if (p->bc != CG_BC_MIRROR && p->bc != CG_BC_CLAMP && p->bc != CG_BC_PERIODIC)
         return fail(CG_EINVAL, "problem %d: unknown boundary mode %d", idx, p->bc);
-    if (p->scheme != CG_EULER && p->scheme != CG_HEUN && p->scheme != CG_RK4)
+    if (p->scheme != CG_EULER && p->scheme != CG_HEUN && p->scheme != CG_RK4 && !gate_scheme(p->scheme))
         return fail(CG_EINVAL, "problem %d: unknown scheme %d", idx, p->scheme);
+    if (gate_scheme(p->scheme) && p->model != CG_BOCF)
+        return fail(CG_EUNSUPPORTED, "problem %d: Rush-Larsen and implicit Euler integrate the gates of the "
+                                     "four-field model only", idx);
+    if ((p->flags & CG_FLAG_TANH_AS_HK) && p->model != CG_BOCF)
+        return fail(CG_EUNSUPPORTED, "problem %d: CG_FLAG_TANH_AS_HK applies to the four-field model only", idx);
+    if (gate_scheme(p->scheme) && p->params) {
+        // the gate coefficients al are negative when these time constants are
+        // positive: tv1m tv2m tvp tw1m tw2m twp ts1 ts2
+        const int tau[] = {6, 7, 8, 9, 10, 13, 21, 22};
+        for (int i : tau)
+            if (!(p->params[i] > 0))
+                return fail(CG_EINVAL, "problem %d: the gate integrators need positive time constants "
+                                       "(param %d = %g)", idx, i, p->params[i]);
+    }
     const int nd = n_diffusive(p->model);
     for (int f = 0; f < 4; ++f) {
         if (!finite(p->Dxx[f]) || !finite(p->Dyy[f]) || p->Dxx[f] < 0 || p->Dyy[f] < 0)
@@ -258,6 +288,13 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         P.mp[cgk::BD_DTW] = prm[10] - prm[9];
         P.mp[cgk::BD_DTSO] = prm[18] - prm[17];
         P.mp[cgk::BD_6K] = 6.0 * k;
+        // tanh variant: H_{kk/3}(u - cc) with t = kk/3 u + 1/2 - kk cc/3
+        P.mp[cgk::BD_KWH] = prm[11] / 3.0;
+        P.mp[cgk::BD_AWH] = 0.5 - prm[11] * prm[12] / 3.0;
+        P.mp[cgk::BD_KSOH] = prm[19] / 3.0;
+        P.mp[cgk::BD_ASOH] = 0.5 - prm[19] * prm[20] / 3.0;
+        P.mp[cgk::BD_KSH] = prm[23] / 3.0;
+        P.mp[cgk::BD_ASH] = 0.5 - prm[23] * prm[24] / 3.0;
         static_assert(cgk::BD_N <= cgk::NMP, "model constant table too small");
         I.mi[0] = I.wc[0];
     }
@@ -400,6 +437,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     P->stencil = p0.stencil;
     P->bc = p0.bc;
     P->scheme = p0.scheme;
+    P->kmodel = kernel_model(p0.model, p0.flags);
     P->nv = n_fields(p0.model);
     P->ns = n_stages(p0.scheme);
     P->flags = p0.flags;
@@ -433,7 +471,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         return fail(CG_EINVAL, "tuning out of range (cells_x 1|2, rows >= 1, threads 128|256|512, "
                                "blocks_per_sm 1..8)");
     }
-    P->kernel = lookup_kernel(P->model, P->stencil, P->scheme, P->cx);
+    P->kernel = lookup_kernel(P->kmodel, P->stencil, P->scheme, P->cx);
     if (!P->kernel) {
         delete P;
         return fail(CG_EUNSUPPORTED, "no kernel for this model/stencil/scheme");
@@ -483,7 +521,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
 
     // Runge-Kutta combine weights (Sect. 3): acc += b_s dt F, Y_{s+1} = z + a dt F
     const double dt = P->dt;
-    if (P->scheme == CG_EULER) {
+    if (P->scheme == CG_EULER || gate_scheme(P->scheme)) {
         P->cacc[0] = dt;
     } else if (P->scheme == CG_HEUN) {
         P->cacc[0] = dt / 2; P->cacc[1] = dt / 2;
@@ -509,6 +547,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg);
         halo_dependencies(nxs, nys, P->nblocks, P->deps);
         P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
+                        P->bc != CG_BC_PERIODIC &&
                         (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
     }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_deps, sizeof(int2) * std::max<size_t>(1, P->deps.size()));
@@ -758,9 +797,10 @@ CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *strea
 
 namespace {
 
-const void *lookup_tlm_kernel(int model, int stencil, int scheme, int cx)
+const void *lookup_tlm_kernel(int kmodel, int stencil, int scheme, int cx)
 {
-    switch (model) {
+    switch (kmodel) {
+    case cgk::MODEL_BOCFH: return cgk::tlm_kernel_bocfh(stencil, scheme, cx);
     case CG_FHN: return cgk::tlm_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::tlm_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::tlm_kernel_diff(stencil, scheme, cx);
@@ -825,6 +865,8 @@ CG_API cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t 
 {
     if (!plan || !bytes || n_tangents < 0) return fail(CG_EINVAL, "bad argument");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    if (gate_scheme(plan->scheme))
+        return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
     *bytes = tlm_layout(plan, n_tangents).total;
     return CG_OK;
 }
@@ -834,6 +876,8 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
 {
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    if (gate_scheme(plan->scheme))
+        return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
     if (!z0 || !zT || !workspace || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
     if (n_tangents > 0 && (!dz0 || !dzT)) return fail(CG_EINVAL, "NULL tangent buffer");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
@@ -857,7 +901,7 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
             e = cudaMemcpyAsync(dzT, dz0, tbytes, cudaMemcpyDeviceToDevice, s);
         return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
     }
-    const void *k = lookup_tlm_kernel(plan->model, plan->stencil, plan->scheme, plan->cx);
+    const void *k = lookup_tlm_kernel(plan->kmodel, plan->stencil, plan->scheme, plan->cx);
     if (!k) return fail(CG_EUNSUPPORTED, "no tangent-linear kernel for this problem");
     st = check_coresident(plan, k);
     if (st != CG_OK) return st;
@@ -881,9 +925,10 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
 
 namespace {
 
-const void *lookup_adj_kernel(int model, int stencil, int scheme, int cx)
+const void *lookup_adj_kernel(int kmodel, int stencil, int scheme, int cx)
 {
-    switch (model) {
+    switch (kmodel) {
+    case cgk::MODEL_BOCFH: return cgk::adj_kernel_bocfh(stencil, scheme, cx);
     case CG_FHN: return cgk::adj_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::adj_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::adj_kernel_diff(stencil, scheme, cx);
@@ -921,6 +966,7 @@ CG_API cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_
 {
     if (!plan || !bytes || n_steps < 0 || checkpoint_every < 0) return fail(CG_EINVAL, "bad argument");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
+    if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
     *bytes = adj_layout(plan, n_steps, checkpoint_every).total;
     return CG_OK;
 }
@@ -930,6 +976,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
 {
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
+    if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
     if (!z0 || !lamT || !lam0 || !dLdD || !workspace || n_steps < 0 || checkpoint_every < 0)
         return fail(CG_EINVAL, "bad argument");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
@@ -957,7 +1004,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
         if (lam0 != lamT) e = cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
         return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
     }
-    const void *ka = lookup_adj_kernel(plan->model, plan->stencil, plan->scheme, plan->cx);
+    const void *ka = lookup_adj_kernel(plan->kmodel, plan->stencil, plan->scheme, plan->cx);
     if (!ka) return fail(CG_EUNSUPPORTED, "no adjoint kernel for this problem");
     st = check_coresident(plan, ka);
     if (st != CG_OK) return st;

@@ -80,13 +80,18 @@ constexpr int MAX_FLAG_BLOCKS = (int)((WS_HEADER - WS_FLAGS_OFF) / 4);
 
 enum { SYNC_GRID = 0, SYNC_NEIGHBOR = 1 };
 
-enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION };
+// MODEL_BOCFH: the four-field model with its tanh terms replaced by smoothed
+// steps (CG_FLAG_TANH_AS_HK); an internal kernel family, not an ABI model id.
+enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION, MODEL_BOCFH = 5 };
 
 // Kernel lookup, one function per model translation unit.  Returns nullptr
 // for an unsupported combination.
 const void *fwd_kernel_fhn(int stencil, int scheme, int cx);
 const void *fwd_kernel_bocf(int stencil, int scheme, int cx);
 const void *fwd_kernel_diff(int stencil, int scheme, int cx);
+const void *fwd_kernel_bocfh(int stencil, int scheme, int cx);
+const void *tlm_kernel_bocfh(int stencil, int scheme, int cx);
+const void *adj_kernel_bocfh(int stencil, int scheme, int cx);
 const void *tlm_kernel_fhn(int stencil, int scheme, int cx);
 const void *tlm_kernel_bocf(int stencil, int scheme, int cx);
 const void *tlm_kernel_diff(int stencil, int scheme, int cx);

@@ -5,8 +5,9 @@
 // every diffusive field; west/east neighbours come from the neighbouring
 // lanes by warp shuffles, the two columns just outside the tile are loaded by
 // lanes 0 and 31.  Ghost points (Fig. 1) are resolved in the load indices:
-// column -1 reads column 1 (MIRROR) or 0 (CLAMP), column nx reads nx-2 or
-// nx-1, and likewise for rows, so no branch touches the arithmetic.
+// column -1 reads column 1 (MIRROR), 0 (CLAMP) or nx-1 (PERIODIC), column nx
+// reads nx-2, nx-1 or 0, and likewise for rows, so no branch touches the
+// arithmetic.
 //
 // Each cell of each stage costs one FMA chain: the model's local terms with
 // the stencil's centre weight folded in, then the off-centre stencil sums,
@@ -264,16 +265,52 @@ enum {
     BD_DTW,            // tw2m - tw1m
     BD_DTSO,           // tso2 - tso1
     BD_6K,             // 6 k
+    BD_KWH,            // kwm / 3        (tanh variant: H_{k/3} in place of (1 + tanh)/2)
+    BD_AWH,            // 1/2 - kwm uwm / 3
+    BD_KSOH,           // kso / 3
+    BD_ASOH,           // 1/2 - kso uso / 3
+    BD_KSH,            // ks / 3
+    BD_ASH,            // 1/2 - ks us / 3
     BD_N
 };
 
-template <> struct Model<MODEL_BOCF> {
+// TH selects the model variant of Sect. 6 in which each (1 + tanh(kk x))/2
+// becomes the smoothed step H_{kk/3}(x) (same value and slope at x = 0).
+template <bool TH> struct BocfModel {
     static constexpr int NV = 4, ND = 1;
     // Stored Jacobian entries (wc_u folded into J_uu):
     // [J_uu, J_uv, J_uw, J_us, J_vu, J_vv, J_wu, J_ww, J_su, J_ss]
     static constexpr int NJ = 10;
     struct Coef { double wc_u; const double *tab; };
     __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.tab}; }
+
+    // (1 + tanh(kk (u - cc)))/2: the sigmoid of 2 kk (u - cc) (constants
+    // ik = 2 kk, ia = -2 kk cc), or H_{kk/3}(u - cc) in the variant
+    // (ihk = kk/3, iha = 1/2 - kk cc/3).  ds times 2 kk is the u-derivative.
+    template <int IA, int IK, int IHA, int IHK>
+    __device__ __forceinline__ static double half_tanh(const double *mp, double u, const double *tab, double &ds)
+    {
+        if constexpr (TH) {
+            const double t = clamp01_int(fma(mp[IHK], u, mp[IHA]));
+            ds = t * (1.0 - t);
+            return (t * t) * fma(-2.0, t, 3.0);
+        } else {
+            return sigmoid(fma(mp[IK], u, mp[IA]), tab, ds);
+        }
+    }
+    template <int IA, int IK, int IHA, int IHK>
+    __device__ __forceinline__ static double half_tanh(const double *mp, double u, const double *tab)
+    {
+        if constexpr (TH) {
+            const double t = clamp01_int(fma(mp[IHK], u, mp[IHA]));
+            return (t * t) * fma(-2.0, t, 3.0);
+        } else {
+            return sigmoid(fma(mp[IK], u, mp[IA]), tab);
+        }
+    }
+#define CG_SW BD_AW2, BD_KW2, BD_AWH, BD_KWH
+#define CG_SSO BD_ASO2, BD_KSO2, BD_ASOH, BD_KSOH
+#define CG_SS BD_AS2, BD_KS2, BD_ASH, BD_KSH
 
     // Shared body: right-hand side t and, when JAC, the Jacobian entries.
     // The three (1 + tanh(k (u - c)))/2 terms are sigmoids of 2 k (u - c)
@@ -302,13 +339,13 @@ template <> struct Model<MODEL_BOCF> {
                 const double Ho = (to * to) * fma(-2.0, to, 3.0);
                 const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
                 const double v_inf = 1.0 - Hvm;
-                const double sw = sigmoid(fma(mp[BD_KW2], u, mp[BD_AW2]), c.tab);
+                const double sw = half_tanh<CG_SW>(mp, u, c.tab);
                 const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
                 const double q = fma(-u, mp[BD_IWINF], 1.0);
                 const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
                 const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
                 const double r_s = fast_rcp(mp[BP_TS1]);
-                const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab);
+                const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
                 const double uo = u - mp[BP_UO];
                 t[0] = fma(c.wc_u, u, -(uo * r_o));
                 t[1] = (v_inf - v) * r_vm;
@@ -319,10 +356,9 @@ template <> struct Model<MODEL_BOCF> {
             if (__all_sync(CG_FULL, bv == ONE && bw == ONE && __double_as_longlong(tvm) == ONE &&
                                         __double_as_longlong(to) == ONE)) {
                 // excited tissue: every switch is 1
-                const double r_so = fast_rcp(fma(mp[BD_DTSO], sigmoid(fma(mp[BD_KSO2], u, mp[BD_ASO2]), c.tab),
-                                                 mp[BP_TSO1]));
+                const double r_so = fast_rcp(fma(mp[BD_DTSO], half_tanh<CG_SSO>(mp, u, c.tab), mp[BP_TSO1]));
                 const double r_s = fast_rcp(fma(1.0, mp[BD_DTS], mp[BP_TS1]));
-                const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab);
+                const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
                 const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u;
                 const double J_fi = -v * (ua * ub) * mp[BD_IFI];
                 const double J_si = -w * (s * mp[BD_ISI]);
@@ -341,15 +377,15 @@ template <> struct Model<MODEL_BOCF> {
         const double r_vm = fast_rcp(tau_vm);
         const double v_inf = 1.0 - Hvm;
         double dsw, dsso, dss;
-        const double sw = sigmoid(fma(mp[BD_KW2], u, mp[BD_AW2]), c.tab, dsw);
+        const double sw = half_tanh<CG_SW>(mp, u, c.tab, dsw);
         const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
         const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-        const double sso = sigmoid(fma(mp[BD_KSO2], u, mp[BD_ASO2]), c.tab, dsso);
+        const double sso = half_tanh<CG_SSO>(mp, u, c.tab, dsso);
         const double r_so = fast_rcp(fma(mp[BD_DTSO], sso, mp[BP_TSO1]));
         const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
-        const double s_inf = sigmoid(fma(mp[BD_KS2], u, mp[BD_AS2]), c.tab, dss);
+        const double s_inf = half_tanh<CG_SS>(mp, u, c.tab, dss);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
         const double omHv = 1.0 - Hv, omHw = 1.0 - Hw;
         const double vinf_v = v_inf - v, winf_w = w_inf - w, sinf_s = s_inf - s;
@@ -417,19 +453,64 @@ template <> struct Model<MODEL_BOCF> {
         t[2] = fma(J[2], k[0], J[7] * k[2]);
         t[3] = fma(J[3], k[0], J[9] * k[3]);
     }
+
+    // For the gate integrators (Rush-Larsen, implicit Euler): t[0] as in
+    // eval and the coefficients of dx/dt = al x + be for x = v, w, s.
+    __device__ static void local_gates(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV],
+                                       double (&al)[3], double (&be)[3])
+    {
+        const double u = z[0], v = z[1], w = z[2], s = z[3];
+        const double k = mp[BP_K];
+        const double tv = clamp01_int(fma(k, u, mp[BD_CV]));
+        const double tw = clamp01_int(fma(k, u, mp[BD_CW]));
+        const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
+        const double to = clamp01_int(fma(k, u, mp[BD_CO]));
+        const double Hv = (tv * tv) * fma(-2.0, tv, 3.0);
+        const double Hw = (tw * tw) * fma(-2.0, tw, 3.0);
+        const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);
+        const double Ho = (to * to) * fma(-2.0, to, 3.0);
+        const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
+        const double v_inf = 1.0 - Hvm;
+        const double r_wm = fast_rcp(fma(mp[BD_DTW], half_tanh<CG_SW>(mp, u, c.tab), mp[BP_TW1M]));
+        const double q = fma(-u, mp[BD_IWINF], 1.0);
+        const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
+        const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
+        const double r_so = fast_rcp(fma(mp[BD_DTSO], half_tanh<CG_SSO>(mp, u, c.tab), mp[BP_TSO1]));
+        const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
+        const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
+        const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
+        const double omHv = 1.0 - Hv, omHw = 1.0 - Hw;
+        const double J_fi = -(v * Hv) * (ua * ub) * mp[BD_IFI];
+        const double J_so = fma(uo * omHw, r_o, Hw * r_so);
+        const double J_si = -(Hw * w) * (s * mp[BD_ISI]);
+        t[0] = fma(c.wc_u, u, -(J_fi + J_so + J_si));
+        t[1] = t[2] = t[3] = 0.0;
+        const double rv = omHv * r_vm, rw = omHw * r_wm;
+        al[0] = -fma(Hv, mp[BD_IVP], rv);
+        be[0] = rv * v_inf;
+        al[1] = -fma(Hw, mp[BD_IWP], rw);
+        be[1] = rw * w_inf;
+        al[2] = -r_s;
+        be[2] = s_inf * r_s;
+    }
 };
+#undef CG_SW
+#undef CG_SSO
+#undef CG_SS
+
+template <> struct Model<MODEL_BOCF> : BocfModel<false> {};
+template <> struct Model<MODEL_BOCFH> : BocfModel<true> {};
 
 // ------------------------------------------------------------- index maps
 
-__device__ __forceinline__ int map_lo(int bc) { return bc == CG_BC_MIRROR ? 1 : 0; }
-
 // Column/row index with ghost resolution: i == -1 and i == n are the ghost
-// points of Fig. 1; i > n is outside every stored cell's stencil and is
-// clamped only to stay in bounds.
+// points of Fig. 1 (MIRROR: 1 and n-2, CLAMP: 0 and n-1, PERIODIC: the
+// opposite edge, n-1 and 0); i > n is outside every stored cell's stencil
+// and is clamped only to stay in bounds.
 __device__ __forceinline__ int map_idx(int i, int n, int bc)
 {
-    if (i < 0) return map_lo(bc);
-    if (i == n) return bc == CG_BC_MIRROR ? n - 2 : n - 1;
+    if (i < 0) return bc == CG_BC_MIRROR ? 1 : (bc == CG_BC_PERIODIC ? n - 1 : 0);
+    if (i == n) return bc == CG_BC_MIRROR ? n - 2 : (bc == CG_BC_PERIODIC ? 0 : n - 1);
     return i < n ? i : n - 1;
 }
 
@@ -496,7 +577,14 @@ struct Bufs {
 // right-hand side D L dz + J dz with J read from jbuf (TANGENT).
 enum { KIND_PRIMAL = 0, KIND_PRIMAL_J = 1, KIND_TANGENT = 2 };
 
-template <int M, int ST, int NS, int CX, int KIND = KIND_PRIMAL>
+// How the non-diffusive gates advance in a one-stage step: with the explicit
+// Euler combine like u, or (Sect. 3, Table 2; four-field model only) by
+// Rush-Larsen, x_inf + (x - x_inf) e^(al dt), or implicit Euler,
+// (x + dt be) / (1 - dt al), from the coefficients of dx/dt = al x + be at
+// the step's starting state.
+enum { GATE_EXPLICIT = 0, GATE_RUSH_LARSEN = 1, GATE_IMPLICIT_EULER = 2 };
+
+template <int M, int ST, int NS, int CX, int KIND = KIND_PRIMAL, int GT = GATE_EXPLICIT>
 struct Stepper {
     using MD = Model<M>;
     static constexpr int NV = MD::NV, ND = MD::ND, NJ = MD::NJ;
@@ -631,8 +719,18 @@ struct Stepper {
 
             // local terms (centre weight folded in)
             double F[CX][NV];
+            double gal[CX][3], gbe[CX][3];       // gate coefficients (GT != GATE_EXPLICIT)
             const int64_t ro_j = (int64_t)y * nx;
-            if constexpr (KIND == KIND_PRIMAL) {
+            if constexpr (KIND == KIND_PRIMAL && GT != GATE_EXPLICIT) {
+                static_assert(NS == 1 && NV == 4 && ND == 1, "gate integrators: one stage, four-field model");
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    double t[NV];
+                    MD::local_gates(coef, mp, zc[c], t, gal[c], gbe[c]);
+#pragma unroll
+                    for (int f = 0; f < NV; ++f) F[c][f] = t[f];
+                }
+            } else if constexpr (KIND == KIND_PRIMAL) {
 #pragma unroll
                 for (int c = 0; c < CX; ++c) {
                     double t[NV];
@@ -697,6 +795,20 @@ struct Stepper {
                 double outv[CX];
 #pragma unroll
                 for (int c = 0; c < CX; ++c) outv[c] = fma(ca, F[c][f], base[c]);
+                if constexpr (GT != GATE_EXPLICIT) {
+                    if (f >= ND) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c) {
+                            const double al = gal[c][f - ND], be = gbe[c][f - ND], x = base[c];
+                            if constexpr (GT == GATE_RUSH_LARSEN) {
+                                const double x_inf = be * fast_rcp(-al);      // al < 0
+                                outv[c] = fma(x - x_inf, exp_neg(al * ca, coef.tab), x_inf);
+                            } else {
+                                outv[c] = fma(ca, be, x) * fast_rcp(fma(-ca, al, 1.0));
+                            }
+                        }
+                    }
+                }
                 store_row((last ? dst : acc) + f * plane + ro, x0, last ? vdst : vacc, own, outv);
                 if (last) {
 #pragma unroll
@@ -745,10 +857,10 @@ struct Stepper {
     }
 };
 
-template <int M, int ST, int NS, int CX>
+template <int M, int ST, int NS, int CX, int GT = GATE_EXPLICIT>
 __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
 {
-    using S = Stepper<M, ST, NS, CX>;
+    using S = Stepper<M, ST, NS, CX, KIND_PRIMAL, GT>;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -829,13 +941,17 @@ template <int M>
 inline const void *pick_fwd_kernel(int stencil, int scheme, int cx)
 {
     if (cx != 1 && cx != 2) return nullptr;
+    constexpr bool gates = (M == MODEL_BOCF || M == MODEL_BOCFH);
 #define CG_K(ST, NS, CXV) reinterpret_cast<const void *>(&k_stage<M, ST, NS, CXV>)
-#define CG_SCH(ST, CXV)                                  \
-    switch (scheme) {                                    \
-    case CG_EULER: return CG_K(ST, 1, CXV);             \
-    case CG_HEUN: return CG_K(ST, 2, CXV);              \
-    case CG_RK4: return CG_K(ST, 4, CXV);               \
-    default: return nullptr;                             \
+#define CG_KG(ST, CXV, GT) reinterpret_cast<const void *>(&k_stage<M, ST, 1, CXV, gates ? GT : GATE_EXPLICIT>)
+#define CG_SCH(ST, CXV)                                                    \
+    switch (scheme) {                                                      \
+    case CG_EULER: return CG_K(ST, 1, CXV);                               \
+    case CG_HEUN: return CG_K(ST, 2, CXV);                                \
+    case CG_RK4: return CG_K(ST, 4, CXV);                                 \
+    case CG_RUSH_LARSEN: return gates ? CG_KG(ST, CXV, GATE_RUSH_LARSEN) : nullptr;        \
+    case CG_IMPLICIT_EULER: return gates ? CG_KG(ST, CXV, GATE_IMPLICIT_EULER) : nullptr;  \
+    default: return nullptr;                                               \
     }
     if (stencil == CG_STENCIL5) {
         if (cx == 1) { CG_SCH(CG_STENCIL5, 1) } else { CG_SCH(CG_STENCIL5, 2) }
@@ -843,6 +959,7 @@ inline const void *pick_fwd_kernel(int stencil, int scheme, int cx)
         if (cx == 1) { CG_SCH(CG_STENCIL9, 1) } else { CG_SCH(CG_STENCIL9, 2) }
     }
 #undef CG_SCH
+#undef CG_KG
 #undef CG_K
     return nullptr;
 }

@@ -17,7 +17,8 @@ def oracle_problem(p):
     return O.problem(_MODEL[p.model], nx=p.nx, ny=p.ny, dx=c.dx, dy=c.dy,
                      Dxx=[c.Dxx[i] for i in range(4)], Dyy=[c.Dyy[i] for i in range(4)],
                      stencil=p.stencil, alpha_d=p.alpha_d, bc=p.bc, scheme=p.scheme, dt=p.dt,
-                     params=None if p.params is None else list(p.params))
+                     params=None if p.params is None else list(p.params),
+                     variant=O.TANH_AS_HK if (p.flags & api.FLAG_TANH_AS_HK) else O.AS_WRITTEN)
 
 
 def oracle_run(p, z0: np.ndarray, n_steps: int) -> np.ndarray:

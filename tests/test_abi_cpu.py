@@ -64,6 +64,9 @@ def _create(prob):
     (dict(scheme=2, dt=5.6e-4), 4),         # RK4 5-point bound 3.71e-4
     (dict(stencil=1, alpha_d=0.4), 1),
     (dict(params=[0.05, 1.5]), 1),
+    (dict(scheme=3), 7), (dict(scheme=4), 7),   # gate integrators: four-field model only
+    (dict(flags=1 << 3), 7),                # tanh variant: four-field model only
+    (dict(bc=3), 1), (dict(scheme=5), 1),
 ])
 def test_validation_errors(L, kw, status):
     from paper_1309_1720_gb300 import Problem
@@ -76,3 +79,11 @@ def test_bocf_gate_diffusion_rejected(L):
     from paper_1309_1720_gb300 import Problem, BOCF
     st, msg = _create(Problem(model=BOCF, dx=0.03, dt=0.05, D=(1e-3, 1e-3)))
     assert st == 7 and "diffuse" in msg
+
+
+def test_gate_integrators_need_positive_time_constants(L):
+    from paper_1309_1720_gb300 import Problem, BOCF, RUSH_LARSEN, default_params
+    prm = default_params(BOCF)
+    prm[8] = -1.0                           # tau_v+ < 0
+    st, msg = _create(Problem(model=BOCF, dx=0.03, dt=0.05, scheme=RUSH_LARSEN, params=prm))
+    assert st == 1 and "positive" in msg
