@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,7 +94,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        out_dir = os.environ.get("CG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
@@ -258,6 +260,19 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "tuning": tun,
                                            "steps_timed": steps, "note": "rate of 500 of the 5000 steps"}
     plan.close()
+    # the same workload with the tanh terms as smoothed steps (Sect. 6 variant;
+    # a different model), and with the gate integrators of Table 2 (one stage
+    # per step: explicit Euler in u, Rush-Larsen / implicit Euler in v, w, s)
+    for name, kw in [("bocf-2048x2048-aniso9pt-rk4-tanh-as-hk", dict(flags=api.FLAG_TANH_AS_HK)),
+                     ("bocf-2048x2048-aniso9pt-rush-larsen", dict(scheme=api.RUSH_LARSEN)),
+                     ("bocf-2048x2048-aniso9pt-implicit-euler", dict(scheme=api.IMPLICIT_EULER))]:
+        q = api.Problem(**{**{k: getattr(p, k) for k in ("model", "nx", "ny", "dx", "D", "Dyy", "stencil",
+                                                            "scheme", "dt", "flags")}, **kw})
+        plan = autotune.plan_for([q], tun)
+        t = timed(plan, z, steps, reps=2)
+        rows[name] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "steps_timed": steps,
+                      "note": "launch shape of the RK4 row"}
+        plan.close()
 
     # 256 uneven instances (64..512, seed 1), 5-point RK4: one persistent
     # launch replayed from a CUDA graph vs 256 sequential single-instance runs
