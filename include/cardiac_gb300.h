@@ -196,6 +196,21 @@ cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_step
 cg_status cg_run_noalloc(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
                          uint32_t *status_dev, void *stream);
 
+/* cg_run for a state held in HOST memory: copies z_in_host to the device,
+ * advances it by n_steps exactly as cg_run does, copies the result to
+ * z_out_host and waits for the stream.  z_in_host and z_out_host are host
+ * buffers in the plan's layout (page-locked memory lets the copies run as
+ * asynchronous DMA; pageable memory works too) and may be the same buffer.
+ * The workspace (device, 256-byte aligned) must hold cg_host_workspace_size
+ * bytes: the cg_run workspace followed by two device copies of the state.
+ * Returns after the result is in z_out_host, with CG_ENAN / CG_ETIMEOUT if
+ * the run recorded a device error (as cg_read_status).  The paper's own
+ * host loop (Matlab driving OpenCL, Sect. 3) moves the state the same way
+ * around each call. */
+cg_status cg_host_workspace_size(cg_plan plan, size_t *bytes);
+cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_out_host, int64_t n_steps,
+                      void *workspace, void *stream);
+
 /* Synchronise the stream and return the device status bits (CG_DEV_*)
  * recorded by the last run that used this workspace.  Returns CG_ENAN or
  * CG_ETIMEOUT when the matching bit is set, CG_OK otherwise. */

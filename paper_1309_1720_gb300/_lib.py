@@ -75,6 +75,9 @@ _SIGS = {
                                 ctypes.c_void_p]),
     "cg_run_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_host_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_run_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_n_fields": (ctypes.c_int32, [ctypes.c_int32]),
     "cg_n_params": (ctypes.c_int32, [ctypes.c_int32]),

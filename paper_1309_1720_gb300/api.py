@@ -134,6 +134,7 @@ class Plan:
         check(L.cg_workspace_size(h, ctypes.byref(sz)))
         self.workspace_bytes = int(sz.value)
         self._ws = None
+        self._host_ws = None
 
     # -- resources
     @property
@@ -181,6 +182,23 @@ class Plan:
         ws = self.workspace() if workspace is None else workspace
         check(_lib.lib().cg_run(self._h, z_in.data_ptr(), out.data_ptr(), int(n_steps), ws.data_ptr(),
                                 _stream_handle(stream)))
+        return out
+
+    def run_host(self, z_in: torch.Tensor, n_steps: int, out: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        """Advance a state held in host memory (a CPU float64 tensor, ideally
+        pinned): copy in, step, copy out, wait.  Returns ``out`` (a CPU
+        tensor, allocated if None; may be ``z_in``)."""
+        assert not z_in.is_cuda and z_in.dtype == torch.float64 and z_in.is_contiguous()
+        assert z_in.numel() == self.offsets[-1]
+        if out is None:
+            out = torch.empty_like(z_in)
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_host_workspace_size(self._h, ctypes.byref(sz)))
+        if self._host_ws is None or self._host_ws.numel() < sz.value:
+            self._host_ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        check(_lib.lib().cg_run_host(self._h, z_in.data_ptr(), out.data_ptr(), int(n_steps),
+                                     self._host_ws.data_ptr(), _stream_handle(stream)))
         return out
 
     def tlm_workspace(self, n_tangents: int) -> torch.Tensor:

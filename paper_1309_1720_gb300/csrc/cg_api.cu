@@ -777,6 +777,43 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     return CG_OK;
 }
 
+// Device state copies of cg_run_host sit after the cg_run workspace.
+static size_t host_state_offset(cg_plan plan)
+{
+    size_t ws = 0;
+    cg_workspace_size(plan, &ws);
+    return (ws + 255) / 256 * 256;
+}
+
+CG_API cg_status cg_host_workspace_size(cg_plan plan, size_t *bytes)
+{
+    if (!plan || !bytes) return fail(CG_EINVAL, "bad argument");
+    const size_t state = ((size_t)plan->offsets.back() * sizeof(double) + 255) / 256 * 256;
+    *bytes = host_state_offset(plan) + 2 * state;
+    return CG_OK;
+}
+
+CG_API cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_out_host, int64_t n_steps,
+                             void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (!z_in_host || !z_out_host || !workspace) return fail(CG_EINVAL, "NULL buffer");
+    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    const size_t nbytes = (size_t)plan->offsets.back() * sizeof(double);
+    char *ws = reinterpret_cast<char *>(workspace);
+    double *d_in = reinterpret_cast<double *>(ws + host_state_offset(plan));
+    double *d_out = reinterpret_cast<double *>(ws + host_state_offset(plan) + (nbytes + 255) / 256 * 256);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_in, z_in_host, nbytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(host to device)");
+    cg_status st = cg_run(plan, d_in, d_out, n_steps, workspace, stream);
+    if (st != CG_OK) return st;
+    e = cudaMemcpyAsync(z_out_host, d_out, nbytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(device to host)");
+    uint32_t flags = 0;
+    return cg_read_status(plan, workspace, stream, &flags);
+}
+
 CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags)
 {
     if (!plan || !workspace || !flags) return fail(CG_EINVAL, "NULL argument");
