@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--profile-case", nargs="?", const="fhn", default=None, choices=["fhn", "bocf"],
                     help="run a short case twice and exit (for ncu captures): 20 steps of the "
                          "1024^2 workload (fhn) or 2 steps of the 2048^2 four-field model (bocf)")
+    ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence"],
+                    help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
 
 
@@ -372,10 +374,135 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     return rows
 
 
+def _fit_slope(xs, ys):
+    """Least-squares slope of log(ys) against log(xs)."""
+    lx, ly = np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float))
+    return float(np.polyfit(lx, ly, 1)[0])
+
+
+def paper_experiments(which):
+    """The measurements of the paper's Sect. 5 on the GB300 stepper, for the
+    two models built here: wall time per unit of simulated time against dt
+    (Fig. 3), against the grid size N (Fig. 4, with the crossover N0 of the
+    fit tau = a max(1, b N^2)), relative L2 accuracy against dt with the
+    observed orders (Fig. 5, Table 2), and cost against accuracy (Fig. 6).
+    Prints one JSON line per experiment."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, api, inputs as I
+
+    def timed_step(plan, z, n, reps=3):
+        out = torch.empty_like(z)
+        plan.run(z, n, out=out)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.run(z, n, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        plan.status()
+        return best / n
+
+    names = {api.EULER: "euler", api.HEUN: "heun", api.RK4: "rk4", api.RUSH_LARSEN: "rush_larsen",
+             api.IMPLICIT_EULER: "implicit_euler"}
+    models = {
+        "fhn": dict(prob=dict(model=api.FHN, dx=0.04), T=0.2, dts=[2e-4, 1e-4, 5e-5, 2.5e-5, 1.25e-5],
+                    schemes=[api.EULER, api.HEUN, api.RK4],
+                    ic=lambda n: I.fhn_broken_wave(n, n, seed=0)),
+        "bocf": dict(prob=dict(model=api.BOCF, dx=0.03, D=(1.171e-3,)), T=10.0,
+                     dts=[0.1, 0.05, 0.025, 0.0125, 0.00625],
+                     schemes=[api.EULER, api.RUSH_LARSEN, api.IMPLICIT_EULER, api.HEUN, api.RK4],
+                     ic=lambda n: I.bocf_spiral_cores(n, n, seed=0)),
+    }
+    n = 256
+    step_time = {}
+    if which in ("all", "timing", "efficiency", "convergence"):
+        res = {}
+        for mname, m in models.items():
+            z = torch.from_numpy(m["ic"](n)).cuda()
+            res[mname] = {}
+            for sc in m["schemes"]:
+                plan = Plan(api.Problem(nx=n, ny=n, scheme=sc, dt=m["dts"][0], **m["prob"]))
+                t = timed_step(plan, z, 2000)
+                plan.close()
+                step_time[(mname, sc)] = t
+                res[mname][names[sc]] = {"us_per_step": 1e6 * t,
+                                         "tau_at_dt": {str(dt): t / dt for dt in m["dts"]}}
+            r = res[mname]
+            r["heun_over_euler"] = r["heun"]["us_per_step"] / r["euler"]["us_per_step"]
+            r["rk4_over_heun"] = r["rk4"]["us_per_step"] / r["heun"]["us_per_step"]
+        if which in ("all", "timing"):
+            print(json.dumps({"experiment": "timing_vs_dt (Fig. 3)", "grid": n, "steps_timed": 2000,
+                              "tau": "device seconds per unit of simulated time = time per step / dt",
+                              "results": res}), flush=True)
+    if which in ("all", "grid"):
+        res = {}
+        Ns = [32, 48, 64, 96, 128, 181, 256, 362, 512, 724, 1024, 1448, 2048, 2896, 4096]
+        for sc in (api.EULER, api.HEUN, api.RK4):
+            ts = []
+            for N in Ns:
+                plan = Plan(api.Problem(model=api.FHN, nx=N, ny=N, dx=0.04, scheme=sc, dt=1e-4))
+                z = torch.from_numpy(I.fhn_broken_wave(N, N, seed=0)).cuda()
+                ts.append(timed_step(plan, z, 2000, reps=2) * 2000)
+                plan.close()
+                del z
+            a = float(np.median(ts[:3]))
+            b = float(np.median([t / N ** 2 for t, N in zip(ts, Ns) if N >= 2048]))
+            res[names[sc]] = {"seconds_2000_steps": dict(zip(map(str, Ns), ts)), "a_s": a, "b_s": b,
+                              "N0": (a / b) ** 0.5,
+                              "gcups_at_4096": 4096 ** 2 * 2000 / ts[-1] / 1e9}
+        print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": "fhn 5-point", "steps": 2000,
+                          "fit": "t = a max(1, (N/N0)^2), a = median of N <= 64, b = a/N0^2 = median t/N^2 "
+                                 "for N >= 2048", "results": res}), flush=True)
+    if which in ("all", "convergence", "efficiency"):
+        conv = {}
+        for mname, m in models.items():
+            z = torch.from_numpy(m["ic"](n)).cuda()
+            T = m["T"]
+            dref = m["dts"][-1] / 8
+            ref_plan = Plan(api.Problem(nx=n, ny=n, scheme=api.RK4, dt=dref, **m["prob"]))
+            ref = ref_plan.run(z, int(round(T / dref)))[0]
+            ref_plan.status()
+            conv[mname] = {}
+            for sc in m["schemes"]:
+                errs = []
+                for dt in m["dts"]:
+                    plan = Plan(api.Problem(nx=n, ny=n, scheme=sc, dt=dt, **m["prob"]))
+                    u = plan.run(z, int(round(T / dt)))[0]
+                    plan.status()
+                    plan.close()
+                    errs.append(float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref)))
+                use = [(d, e) for d, e in zip(m["dts"], errs) if e > 1e-13]
+                alpha = _fit_slope(*zip(*use)) if len(use) >= 2 else None
+                cost = [step_time[(mname, sc)] / d for d in m["dts"]]
+                conv[mname][names[sc]] = {"dt": m["dts"], "Delta": errs, "alpha": alpha, "tau": cost}
+            # cost of reaching Delta = 1e-7 from each method's power law
+            target = 1e-7
+            at = {}
+            for sc in m["schemes"]:
+                c = conv[mname][names[sc]]
+                pts = [(d, e) for d, e in zip(c["dt"], c["Delta"]) if e > 1e-13]
+                if c["alpha"] and len(pts) >= 2:
+                    d0, e0 = pts[-1]
+                    dt_t = d0 * (target / e0) ** (1.0 / c["alpha"])
+                    at[names[sc]] = step_time[(mname, sc)] / dt_t
+            conv[mname]["tau_at_Delta_1e-7"] = at
+            if "rk4" in at:
+                conv[mname]["rk4_speedup_at_1e-7"] = {k: v / at["rk4"] for k, v in at.items() if k != "rk4"}
+        print(json.dumps({"experiment": "accuracy_vs_dt and cost_vs_accuracy (Figs. 5, 6, Table 2)",
+                          "grid": n, "Delta": "relative L2 error of u against RK4 at dt/8 of the finest dt",
+                          "T": {k: m["T"] for k, m in models.items()}, "results": conv}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.experiment:
+        paper_experiments(args.experiment)
         return
     ws, rank, local = dist_env()
     import torch
