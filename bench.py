@@ -42,7 +42,7 @@ BYTES_PER_CELL_UPDATE = 32
 # dram__bytes_write.sum) on a 20-step launch of this workload; traffic grows
 # in proportion to the steps of a launch (L2 write-backs of the resident
 # working set), so one bench launch moves this times its cell-updates.
-MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 35.4
+MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 35.9
 
 
 def parse():
@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None, choices=["fhn", "bocf"],
+    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None, choices=["fhn", "bocf", "tlm", "adj"],
                     help="run a short case twice and exit (for ncu captures): 20 steps of the "
-                         "1024^2 workload (fhn) or 2 steps of the 2048^2 four-field model (bocf)")
+                         "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), or on "
+                         "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
+                         "16 steps (adj)")
     ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
@@ -530,6 +532,22 @@ def main():
     out = torch.empty_like(z0)
     ws_t = plan.workspace()
 
+    if args.profile_case in ("tlm", "adj"):
+        n = 512
+        gp = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, scheme=api.RK4, dt=2.5e-4)
+        plan = Plan(gp)
+        z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
+        for _ in range(2):
+            if args.profile_case == "tlm":
+                dz0 = torch.from_numpy(np.stack([I.unit_direction(z.shape, 2, offset=i * z.numel())
+                                                 for i in range(64)])).cuda()
+                plan.tlm(z, dz0, 4)
+            else:
+                plan.adjoint(z, z.clone(), 16)
+        plan.status()
+        torch.cuda.synchronize()
+        print("profile case done")
+        return
     if args.profile_case:
         if args.profile_case == "bocf":
             # four-field 2048^2 anisotropic 9-point RK4: 640 MB working set

@@ -149,7 +149,11 @@ struct Adjoint {
             const bool bnd = yedge || xedge;      // warp-uniform: some cell of this row may sit on the boundary
             double wcell[CX];
 #pragma unroll
-            for (int c = 0; c < CX; ++c) wcell[c] = (yedge ? 0.5 : 1.0) * (mirror ? wcol[c] : 1.0);
+            for (int c = 0; c < CX; ++c) wcell[c] = 1.0;
+            if (bnd) {
+#pragma unroll
+                for (int c = 0; c < CX; ++c) wcell[c] = (yedge ? 0.5 : 1.0) * (mirror ? wcol[c] : 1.0);
+            }
 
             // primal stage input and kbar at the cells
             double yc[CX][NV], kc[CX][NV];
@@ -160,8 +164,14 @@ struct Adjoint {
 #pragma unroll
                 for (int c = 0; c < CX; ++c) yc[c][f] = v[c];
                 if (f < ND) {
+                    // boundary rows/columns only (warp-uniform branch, so the
+                    // interior does not pay for the multiplies)
 #pragma unroll
-                    for (int c = 0; c < CX; ++c) kc[c][f] = bnd ? mid[f < ND ? f : 0][c] * wcell[c] : mid[f < ND ? f : 0][c];
+                    for (int c = 0; c < CX; ++c) kc[c][f] = mid[f < ND ? f : 0][c];
+                    if (bnd) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c) kc[c][f] *= wcell[c];
+                    }
                 } else {
                     SP::load_row(Kin + f * plane, nx, y, cx, hx, vk, false, v, dummy);
 #pragma unroll
@@ -187,9 +197,13 @@ struct Adjoint {
 #pragma unroll
                 for (int c = 0; c < CX; ++c) So[c] = 0.0;
                 add_offcentre<ST, CX>(lane, lo[f], mid[f], hi[f], hlo[f], hmid[f], hhi[f], wx[f], wy[f], wd[f], So);
+                if (bnd) {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) So[c] *= wcell[c];
+                }
 #pragma unroll
                 for (int c = 0; c < CX; ++c) {
-                    const double Sw = bnd ? So[c] * wcell[c] : So[c];
+                    const double Sw = So[c];
                     F[c][f] += Sw;
                     const double lt = fma(wcf[f], kc[c][f], Sw);        // ((D L)^T kbar)_f at the cell
                     if (own & (1u << c)) dd[f] = fma(yc[c][f], lt, dd[f]);
@@ -251,9 +265,15 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const double *mp = a.mp;
-    const Inst &I = a.inst[0];
     const int gw = blockIdx.x * nwarps + warp;
     const int sbeg = a.warp_seg[gw], send = a.warp_seg[gw + 1];
+    __shared__ SegCache s_cache[MAX_WARPS];
+    SegCache &cache = s_cache[warp];
+    fill_seg_cache(cache, a, sbeg, send, lane);
+    __shared__ Inst s_inst;                  // the single instance (see SegCache)
+    if (threadIdx.x == 0) s_inst = a.inst[0];
+    __syncthreads();
+    const Inst &I = s_inst;
     uint32_t bad = 0;
     double dd[ND > 0 ? ND : 1];
 #pragma unroll
@@ -263,7 +283,7 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
         const int64_t k = b.m - 1 - g / NS;
         const int s = NS - 1 - (int)(g % NS);
         for (int q = sbeg; q < send; ++q) {
-            const Seg sg = a.segs[q];
+            const Seg sg = (q - sbeg) < SEG_CACHE ? cache.seg[q - sbeg] : a.segs[q];
             bad |= AD::seg(a, b, I, mp, sg, k, s, b.r0 + g, lane, dd);
         }
     };

