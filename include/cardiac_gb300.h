@@ -176,6 +176,20 @@ cg_status cg_workspace_size(cg_plan plan, size_t *bytes);
 cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
                  void *workspace, void *stream);
 
+/* cg_run for a batch plan whose instances live in separate caller buffers:
+ * z_in and z_out are HOST arrays of cg_plan_n_instances(plan) DEVICE
+ * pointers, entry i the state of instance i (user order) in the
+ * [n_v][ny][nx] layout, 8-byte aligned.  z_in[i] == z_out[i] steps instance
+ * i in place; otherwise its two buffers must not overlap (buffers of
+ * different instances are not checked against each other and must not
+ * overlap).  The pointer arrays are read during the call only (they are
+ * written into the workspace by a kernel launch, so the call can be
+ * captured into a CUDA graph, which then replays with these pointers).
+ * Same workspace (cg_workspace_size), status word and results as cg_run on
+ * the packed layout. */
+cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *const *z_out, int64_t n_steps,
+                       void *workspace, void *stream);
+
 /* Same as cg_run, for callers that cannot allocate device memory when they
  * step: code running while a stream is captured into a CUDA graph (where
  * allocation is not allowed), programs whose device memory belongs to their
@@ -195,6 +209,15 @@ cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_step
  * once the run has finished on the stream. */
 cg_status cg_run_noalloc(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
                          uint32_t *status_dev, void *stream);
+
+/* The right-hand side F(z) = D L z + N[z] of Eq. (rdeqn) (stencil, ghosts
+ * and local terms exactly as the steps use them) for the plan's state z
+ * (device, plan layout, packed for a batch) into f (device, same layout, not
+ * overlapping z).  Asynchronous; clears the device status word, which
+ * records non-finite values of f.  Valid for every scheme (it evaluates F,
+ * no integrator).  Newton-Krylov solvers for periodic orbits need it for the
+ * phase condition and the derivative of the flow map in the period. */
+cg_status cg_rhs(cg_plan plan, const double *z, double *f, void *workspace, void *stream);
 
 /* cg_run for a state held in HOST memory: copies z_in_host to the device,
  * advances it by n_steps exactly as cg_run does, copies the result to

@@ -184,6 +184,31 @@ class Plan:
                                 _stream_handle(stream)))
         return out
 
+    def rhs(self, z: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """F(z) = D L z + N[z], the right-hand side the steps integrate."""
+        assert z.is_cuda and z.dtype == torch.float64 and z.is_contiguous()
+        assert z.numel() == self.offsets[-1]
+        out = torch.empty_like(z) if out is None else out
+        check(_lib.lib().cg_rhs(self._h, z.data_ptr(), out.data_ptr(), self.workspace().data_ptr(),
+                                _stream_handle(stream)))
+        return out
+
+    def run_batch(self, states, n_steps: int, outs=None, stream=None):
+        """Advance each instance in its own device tensor (``states[i]`` of
+        shape [n_v, ny, nx]); returns the output tensors (``outs`` or new ones;
+        ``outs[i] is states[i]`` steps in place)."""
+        n = len(self.problems)
+        assert len(states) == n
+        for i, z in enumerate(states):
+            assert z.is_cuda and z.dtype == torch.float64 and z.is_contiguous()
+            assert z.numel() == self.offsets[i + 1] - self.offsets[i]
+        outs = [torch.empty_like(z) for z in states] if outs is None else list(outs)
+        pin = (ctypes.c_void_p * n)(*[z.data_ptr() for z in states])
+        pout = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        ws = self.workspace()
+        check(_lib.lib().cg_batch_run(self._h, pin, pout, int(n_steps), ws.data_ptr(), _stream_handle(stream)))
+        return outs
+
     def run_host(self, z_in: torch.Tensor, n_steps: int, out: Optional[torch.Tensor] = None,
                  stream=None) -> torch.Tensor:
         """Advance a state held in host memory (a CPU float64 tensor, ideally

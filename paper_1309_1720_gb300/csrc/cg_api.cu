@@ -139,8 +139,17 @@ struct cg_plan_s {
     std::vector<int2> deps;          // halo owners of each block (neighbour sync)
     int2 *d_deps = nullptr;
     int32_t sync_mode = cgk::SYNC_GRID;
-    double *d_tab = nullptr;         // 2^(j/32) table of the exponential
+    double *d_tab = nullptr;         // 2^(j/256) table of the exponential
 };
+
+namespace cgk {
+
+void exp_table(double *tab, int n)
+{
+    for (int j = 0; j < n; ++j) tab[j] = (double)std::exp2((long double)j / (long double)n);
+}
+
+}  // namespace cgk
 
 namespace {
 
@@ -556,10 +565,10 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     if (e == cudaSuccess) e = cudaMalloc(&P->d_deps, sizeof(int2) * std::max<size_t>(1, P->deps.size()));
     if (e == cudaSuccess && !P->deps.empty())
         e = cudaMemcpy(P->d_deps, P->deps.data(), sizeof(int2) * P->deps.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_tab, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_tab, sizeof(double) * cgk::EXP_TAB);
     if (e == cudaSuccess) {
-        double tab[32];                       // 2^(j/32), rounded once from extended precision
-        for (int j = 0; j < 32; ++j) tab[j] = (double)std::exp2((long double)j / 32.0L);
+        double tab[cgk::EXP_TAB];
+        cgk::exp_table(tab, cgk::EXP_TAB);
         e = cudaMemcpy(P->d_tab, tab, sizeof tab, cudaMemcpyHostToDevice);
         for (Inst &I : P->inst) I.tab = P->d_tab;
     }
@@ -701,12 +710,140 @@ CG_API cg_status cg_plan_destroy(cg_plan plan)
     return CG_OK;
 }
 
+// Bytes of the per-instance pointer tables of cg_batch_run at the end of
+// the workspace (input then output pointers, plan order).
+static size_t ptr_table_bytes(cg_plan plan)
+{
+    return (2 * plan->inst.size() * sizeof(void *) + 255) / 256 * 256;
+}
+
+static size_t ptr_table_offset(cg_plan plan)
+{
+    return (cgk::WS_HEADER + (size_t)plan->scratch_elems * sizeof(double) + 255) / 256 * 256;
+}
+
 CG_API cg_status cg_workspace_size(cg_plan plan, size_t *bytes)
 {
     if (!plan || !bytes) return fail(CG_EINVAL, "NULL argument");
-    *bytes = cgk::WS_HEADER + (size_t)plan->scratch_elems * sizeof(double);
+    *bytes = ptr_table_offset(plan) + ptr_table_bytes(plan);
     return CG_OK;
 }
+
+namespace {
+
+// Up to 120 pointers written into a device table by one launch (the values
+// travel in the kernel's parameters, so the call can be graph-captured).
+struct PtrChunk {
+    const double *p[120];
+    int32_t n, base;
+};
+
+__global__ void k_set_ptrs(const double **dst, PtrChunk c)
+{
+    const int i = threadIdx.x;
+    if (i < c.n) dst[c.base + i] = c.p[i];
+}
+
+// Shared body of cg_run (packed state: z_in, z_out) and cg_batch_run
+// (per-instance buffers in user order: zin_u, zout_u).
+cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double *const *zin_u,
+                   double *const *zout_u, int64_t n_steps, void *workspace, void *stream)
+{
+    const bool tab = (zin_u != nullptr);
+    const size_t n_inst = plan->inst.size();
+    cg_status st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    // per-instance buffers in plan order, and whether any is stepped in place
+    std::vector<const double *> pin(n_inst);
+    std::vector<double *> pout(n_inst);
+    bool any_alias = false;
+    for (size_t i = 0; i < n_inst; ++i) {
+        const size_t k = (size_t)plan->order[i];
+        pin[k] = tab ? zin_u[i] : z_in + plan->inst[k].off;
+        pout[k] = tab ? zout_u[i] : z_out + plan->inst[k].off;
+        any_alias |= (pin[k] == pout[k]);
+    }
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    auto inst_bytes = [&](size_t k) {
+        const Inst &I = plan->inst[k];
+        return sizeof(double) * (size_t)plan->nv * I.nx * I.ny;
+    };
+    if (n_steps == 0) {
+        for (size_t k = 0; k < n_inst; ++k) {
+            if (pin[k] == pout[k]) continue;
+            e = cudaMemcpyAsync(pout[k], pin[k], inst_bytes(k), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        return CG_OK;
+    }
+
+    RunArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = plan->d_inst;
+    a.segs = plan->d_segs;
+    a.warp_seg = plan->d_warp_seg;
+    a.sched = plan->sched;
+    const cg_plan_s *P = plan;
+    a.n_inst = (int32_t)n_inst;
+    a.n_tiles = plan->n_tiles;
+    a.bc = plan->bc;
+    a.rows = plan->rows;
+    a.z_in = z_in;
+    a.z_out = z_out;
+    if (tab) {
+        double **t = reinterpret_cast<double **>(ws + ptr_table_offset(plan));
+        for (size_t b0 = 0; b0 < 2 * n_inst; b0 += 120) {
+            PtrChunk c;
+            std::memset(&c, 0, sizeof c);
+            c.base = (int32_t)b0;
+            c.n = (int32_t)std::min<size_t>(120, 2 * n_inst - b0);
+            for (int j = 0; j < c.n; ++j) {
+                const size_t q = b0 + j;
+                c.p[j] = q < n_inst ? pin[q] : pout[q - n_inst];
+            }
+            k_set_ptrs<<<1, 128, 0, s>>>(const_cast<const double **>(t), c);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "pointer table");
+        }
+        a.zin_tab = t;
+        a.zout_tab = t + n_inst;
+    }
+    a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
+    a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
+    a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
+    a.flags = reinterpret_cast<unsigned *>(ws + cgk::WS_FLAGS_OFF);
+    a.deps = P->d_deps;
+    a.sync_mode = P->sync_mode;
+    // one-stage steps in place would overwrite their own input: alternate
+    // through the scratch copy, starting there (parity 1)
+    const bool alias_single_stage = (plan->ns == 1) && any_alias;
+    a.parity = alias_single_stage ? 1 : (int32_t)((n_steps - 1) & 1);
+    a.timeout_ns = plan->timeout_ns;
+    std::memcpy(a.cacc, plan->cacc, sizeof a.cacc);
+    std::memcpy(a.cy, plan->cy, sizeof a.cy);
+    std::memcpy(a.mp, plan->mp, sizeof a.mp);
+    const int64_t G = n_steps * plan->ns;
+    void *args[] = {&a};
+
+    const int wpb = plan->threads / 32;
+    const int qgrid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
+    st = launch_stages(plan, plan->kernel, args, a, 0, G, qgrid, s);
+    if (st != CG_OK) return st;
+    if (alias_single_stage && (n_steps & 1)) {
+        // odd number of single-stage steps: the last result sits in the
+        // scratch copy of each instance
+        for (size_t k = 0; k < n_inst; ++k) {
+            e = cudaMemcpyAsync(pout[k], a.ws + plan->inst[k].ws_off, inst_bytes(k), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
+        }
+    }
+    return CG_OK;
+}
+
+}  // namespace
 
 CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps, void *workspace,
                         void *stream)
@@ -724,62 +861,79 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
         const char *a0 = reinterpret_cast<const char *>(z_in), *b0 = reinterpret_cast<const char *>(z_out);
         if (a0 < b0 + nbytes && b0 < a0 + nbytes) return fail(CG_EINVAL, "z_in and z_out partially overlap");
     }
+    return run_impl(plan, z_in, z_out, nullptr, nullptr, n_steps, workspace, stream);
+}
+
+CG_API cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *const *z_out, int64_t n_steps,
+                              void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
+    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    for (size_t i = 0; i < plan->inst.size(); ++i) {
+        if (!z_in[i] || !z_out[i]) return fail(CG_EINVAL, "instance %zu: NULL buffer", i);
+        if ((reinterpret_cast<uintptr_t>(z_in[i]) & 7) || (reinterpret_cast<uintptr_t>(z_out[i]) & 7))
+            return fail(CG_EINVAL, "instance %zu: state buffers must be 8-byte aligned", i);
+        const size_t nb = (size_t)(plan->offsets[i + 1] - plan->offsets[i]) * sizeof(double);
+        const char *a0 = reinterpret_cast<const char *>(z_in[i]), *b0 = reinterpret_cast<const char *>(z_out[i]);
+        if (a0 != b0 && a0 < b0 + nb && b0 < a0 + nb)
+            return fail(CG_EINVAL, "instance %zu: z_in and z_out partially overlap", i);
+    }
+    return run_impl(plan, nullptr, nullptr, z_in, z_out, n_steps, workspace, stream);
+}
+
+CG_API cg_status cg_rhs(cg_plan plan, const double *z, double *f, void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (!z || !f || !workspace) return fail(CG_EINVAL, "NULL buffer");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(z) & 7) || (reinterpret_cast<uintptr_t>(f) & 7))
+        return fail(CG_EINVAL, "state buffers must be 8-byte aligned");
+    const size_t nbytes = (size_t)plan->offsets.back() * sizeof(double);
+    const char *a0 = reinterpret_cast<const char *>(z), *b0 = reinterpret_cast<const char *>(f);
+    if (a0 < b0 + nbytes && b0 < a0 + nbytes) return fail(CG_EINVAL, "z and f overlap");
     cg_status st = check_plan_device(plan);
     if (st != CG_OK) return st;
+    // the one-stage (explicit Euler) kernel of the plan's model, stencil and
+    // tile width, writing F itself
+    const void *k = lookup_kernel(plan->kmodel, plan->stencil, CG_EULER, plan->cx);
+    if (!k) return fail(CG_EUNSUPPORTED, "no kernel for this model/stencil");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(workspace);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
-    if (n_steps == 0) {
-        if (z_in != z_out) {
-            e = cudaMemcpyAsync(z_out, z_in, nbytes, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-        }
-        return CG_OK;
-    }
-
     RunArgs a;
     std::memset(&a, 0, sizeof a);
     a.inst = plan->d_inst;
     a.segs = plan->d_segs;
     a.warp_seg = plan->d_warp_seg;
     a.sched = plan->sched;
-    const cg_plan_s *P = plan;
     a.n_inst = (int32_t)plan->inst.size();
     a.n_tiles = plan->n_tiles;
     a.bc = plan->bc;
     a.rows = plan->rows;
-    a.z_in = z_in;
-    a.z_out = z_out;
+    a.z_in = z;
+    a.z_out = f;
     a.ws = reinterpret_cast<double *>(ws + cgk::WS_HEADER);
     a.sync = reinterpret_cast<unsigned *>(ws + cgk::WS_SYNC_OFF);
     a.status = reinterpret_cast<uint32_t *>(ws + cgk::WS_STATUS_OFF);
     a.flags = reinterpret_cast<unsigned *>(ws + cgk::WS_FLAGS_OFF);
-    a.deps = P->d_deps;
-    a.sync_mode = P->sync_mode;
-    const bool alias_single_stage = (plan->ns == 1) && (z_in == z_out);
-    a.parity = alias_single_stage ? 1 : (int32_t)((n_steps - 1) & 1);
+    a.deps = plan->d_deps;
     a.timeout_ns = plan->timeout_ns;
-    std::memcpy(a.cacc, plan->cacc, sizeof a.cacc);
-    std::memcpy(a.cy, plan->cy, sizeof a.cy);
+    a.rhs_only = 1;
+    a.persistent = 0;
+    a.g_begin = 0;
+    a.g_end = 1;
+    a.cacc[0] = 1.0;
     std::memcpy(a.mp, plan->mp, sizeof a.mp);
-    const int64_t G = n_steps * plan->ns;
     void *args[] = {&a};
-
     const int wpb = plan->threads / 32;
-    const int qgrid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
-    st = launch_stages(plan, plan->kernel, args, a, 0, G, qgrid, s);
-    if (st != CG_OK) return st;
-    if (alias_single_stage && (n_steps & 1)) {
-        // odd number of single-stage steps in place: the last result sits in
-        // the scratch copy of each instance
-        for (size_t k = 0; k < plan->inst.size(); ++k) {
-            const Inst &I = plan->inst[k];
-            e = cudaMemcpyAsync(z_out + I.off, a.ws + I.ws_off,
-                                sizeof(double) * (size_t)plan->nv * I.nx * I.ny, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
-        }
-    }
+    const int grid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
+    e = cudaLaunchKernel(k, dim3(grid), dim3(plan->threads), args, 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs kernel launch");
     return CG_OK;
 }
 

@@ -10,17 +10,19 @@
 //
 // exp_neg: e^x for x <= 0, by P. T. P. Tang's table-driven method ("Table-
 // driven implementation of the exponential function in IEEE floating-point
-// arithmetic", ACM TOMS 15, 1989): x = (32 m + j) ln2/32 + r with
-// |r| <= ln2/64, e^x = 2^m 2^(j/32) e^r, e^r - 1 by its Taylor polynomial of
-// degree 6 (remainder < 4e-18), 2^(j/32) from a 32-entry table, 2^m added to
-// the exponent field.  Eleven FP64 instructions.
-//
+// arithmetic", ACM TOMS 15, 1989) with a 256-entry table:
+// x = (256 m + j) ln2/256 + r with |r| <= ln2/512, e^x = 2^m 2^(j/256) e^r,
+// e^r - 1 by its Taylor polynomial of degree 4 (remainder below
+// |r|^5/120 < 4e-17), 2^(j/256) from the table, 2^m added to the exponent
+// field.  Nine FP64 instructions.
 // sigmoid: 1/(1 + e^-a) = (1 + tanh(a/2))/2 from e = e^-|a| in (0, 1]:
-// 1/(1+e) for a >= 0, e/(1+e) otherwise.  Sixteen FP64 instructions; also
+// 1/(1+e) for a >= 0, e/(1+e) otherwise.  Fourteen FP64 instructions; also
 // returns s (1 - s) = e/(1+e)^2 for derivatives.
 #pragma once
 
 #include <cstdint>
+
+#include "cg_internal.h"
 
 namespace cgk {
 
@@ -42,7 +44,7 @@ __device__ __forceinline__ double fast_rcp(double x)
     return fma(r, fma(e, e, e), r);
 }
 
-// e^x for x <= 0 (x below -708 is treated as -708); tab[j] = 2^(j/32).
+// e^x for x <= 0 (x below -708 is treated as -708); tab[j] = 2^(j/256).
 __device__ __forceinline__ double exp_neg(double x, const double *tab)
 {
     const long long LIM = 0x4086200000000000ll;             // 708.0
@@ -50,23 +52,21 @@ __device__ __forceinline__ double exp_neg(double x, const double *tab)
     b = b > LIM ? LIM : b;
     x = -__longlong_as_double(b);
     const double SHIFT = 6755399441055744.0;                // 1.5 * 2^52: rounds to an integer
-    const double INV_L = 46.16624130844683;                 // 32 / ln 2
-    const double L_HI = 0.02166084939249829;                // ln 2 / 32, leading part
-    const double L_LO = 7.247021293269686e-19;              // ln 2 / 32 - L_HI
+    const double INV_L = 369.3299304675746;                 // 256 / ln 2
+    const double L_HI = 0.0027076061740622863;              // ln 2 / 256, leading part
+    const double L_LO = 9.058776616587108e-20;              // ln 2 / 256 - L_HI
     const double t = fma(x, INV_L, SHIFT);
-    const long long n = __double_as_longlong(t) - 0x4338000000000000ll;   // round(x 32 / ln 2)
+    const long long n = __double_as_longlong(t) - 0x4338000000000000ll;   // round(x 256 / ln 2)
     const double kd = t - SHIFT;
     double r = fma(-kd, L_HI, x);
     r = fma(-kd, L_LO, r);
-    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-    q = fma(r, q, 1.0 / 24.0);
-    q = fma(r, q, 1.0 / 6.0);
+    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     q = fma(r, q, 0.5);
     q = fma(r, q, 1.0);
     const double p = r * q;                                  // e^r - 1
-    const double T = __ldg(tab + (n & 31));
+    const double T = __ldg(tab + (n & (EXP_TAB - 1)));
     const double e = fma(T, p, T);
-    return __longlong_as_double(__double_as_longlong(e) + ((n >> 5) << 52));
+    return __longlong_as_double(__double_as_longlong(e) + ((n >> 8) << 52));
 }
 
 // s = 1 / (1 + e^-a); ds = s (1 - s).

@@ -11,6 +11,7 @@ namespace cgk {
 
 constexpr int MAXF = 4;     // fields per cell (BOCF: u, v, w, s)
 constexpr int NMP = 56;     // model constants shared by all instances of a plan
+constexpr int EXP_TAB = 256; // entries 2^(j/256) of the exponential's table (cg_fastmath.cuh)
 
 // One grid instance, resident in a plan-owned device table.  Coefficients
 // carry D/dx^2 and the stencil weights; the centre weight is folded into the
@@ -25,7 +26,7 @@ struct Inst {
     double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights
     double wt[MAXF];         // wy / wd (0 where wd = 0): the 9-point stencil's row-sum form
     double mi[4];            // instance-dependent folds of centre weight and model constants
-    const double *tab;       // plan-owned table 2^(j/32), j = 0..31 (exponentials)
+    const double *tab;       // plan-owned table 2^(j/256), j = 0..255 (exponentials)
 };
 
 // A warp's share of one stage under the static schedule: columns
@@ -50,6 +51,8 @@ struct RunArgs {
     int32_t bc, rows;            // ghost mode, rows per warp tile
     const double *z_in;
     double *z_out;
+    const double *const *zin_tab;   // optional per-instance input/output pointers (plan order);
+    double *const *zout_tab;        // when set they replace z_in + off and z_out + off
     double *ws;                  // base of the per-instance scratch blocks
     double *store;               // optional: keep every stage input (single instance; see Bufs)
     unsigned *flags;             // per-block count of finished stages (neighbour sync)
@@ -61,6 +64,7 @@ struct RunArgs {
     int64_t g_begin, g_end;      // global stage range [g_begin, g_end) of this launch
     int32_t parity;              // step k stores its result in z_out iff (k + parity) is even
     int32_t persistent;          // 1: loop over stages with grid barriers; 0: one stage
+    int32_t rhs_only;            // 1: write F(z) = D L z + N[z] itself to z_out (one-stage kernels)
     uint32_t nblocks_expect;     // arrivals the grid barrier waits for
     uint32_t stuck_barrier;      // testing knob: first barrier waits for one extra block
     uint64_t timeout_ns;         // bound on a barrier wait
@@ -99,6 +103,10 @@ const void *tlm_kernel_diff(int stencil, int scheme, int cx);
 const void *adj_kernel_fhn(int stencil, int scheme, int cx);
 const void *adj_kernel_bocf(int stencil, int scheme, int cx);
 const void *adj_kernel_diff(int stencil, int scheme, int cx);
+
+// Host: fill tab[j] = 2^(j / n), j = 0..n-1, each rounded once to double
+// from extended precision (the exponential's table).
+void exp_table(double *tab, int n);
 
 // Record a message for cg_last_error() on the calling thread; returns st.
 cg_status set_last_error(cg_status st, const char *msg);

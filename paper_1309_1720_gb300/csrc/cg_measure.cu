@@ -120,8 +120,8 @@ __global__ void k_check_fastmath(int fn, const double *x, double *own, double *r
 CG_API cg_status cg_check_fastmath(int32_t fn, const double *x, double *own, double *ref, int64_t n)
 {
     if (fn < 0 || fn > 2 || !x || !own || !ref || n < 0) return CG_EINVAL;
-    double tab[32];
-    for (int j = 0; j < 32; ++j) tab[j] = (double)std::exp2((long double)j / 32.0L);
+    double tab[cgk::EXP_TAB];
+    cgk::exp_table(tab, cgk::EXP_TAB);
     double *dtab = nullptr;
     cudaError_t e = cudaMalloc(&dtab, sizeof tab);
     if (e == cudaSuccess) e = cudaMemcpy(dtab, tab, sizeof tab, cudaMemcpyHostToDevice);

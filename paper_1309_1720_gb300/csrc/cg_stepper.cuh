@@ -603,6 +603,14 @@ struct Bufs {
     double *store = nullptr;
 };
 
+// Buffers of instance i (plan order): its slice of the packed state, or the
+// caller's own per-instance buffers when the launch carries pointer tables.
+__device__ __forceinline__ Bufs inst_bufs(const RunArgs &a, const Inst &I, int i)
+{
+    if (a.zin_tab != nullptr) return Bufs{a.zin_tab[i], a.zout_tab[i], a.ws + I.ws_off, a.store};
+    return Bufs{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, a.store};
+}
+
 // What a sweep computes: the model's right-hand side (PRIMAL), the same plus
 // the local Jacobian dN/dz written to jbuf (PRIMAL_J), or the tangent-linear
 // right-hand side D L dz + J dz with J read from jbuf (TANGENT).
@@ -847,7 +855,7 @@ struct Stepper {
                 }
                 double outv[CX];
 #pragma unroll
-                for (int c = 0; c < CX; ++c) outv[c] = fma(ca, F[c][f], base[c]);
+                for (int c = 0; c < CX; ++c) outv[c] = a.rhs_only ? F[c][f] : fma(ca, F[c][f], base[c]);
                 if constexpr (GT != GATE_EXPLICIT) {
                     if (f >= ND) {
 #pragma unroll
@@ -904,13 +912,13 @@ struct Stepper {
     }
 
     // Queue tile lt of instance I: rows [ty*rows, ...) x columns of tile tx.
-    __device__ __forceinline__ static uint32_t tile(const RunArgs &a, const Inst &I, const double *mp, int lt,
-                                                    int s, int64_t step, int lane)
+    __device__ __forceinline__ static uint32_t tile(const RunArgs &a, const Inst &I, int i, const double *mp,
+                                                    int lt, int s, int64_t step, int lane)
     {
         const int tx = lt % I.tiles_x, ty = lt / I.tiles_x;
         const int y0 = ty * a.rows;
         const int y1 = min(y0 + a.rows, I.ny) - 1;
-        const Bufs B{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, a.store};
+        const Bufs B = inst_bufs(a, I, i);
         return seg(a, I, mp, B, nullptr, tx * 32 * CX, y0, y1, -1, 0, 0, -1, 0, 0, s, step, lane);
     }
 };
@@ -925,6 +933,7 @@ constexpr int MAX_WARPS = 16;          // 512 threads per block at most
 struct SegCache {
     Seg seg[SEG_CACHE];
     Inst inst[SEG_CACHE];
+    Bufs bufs[SEG_CACHE];
 };
 
 __device__ __forceinline__ void fill_seg_cache(SegCache &c, const RunArgs &a, int sbeg, int send, int lane)
@@ -933,6 +942,7 @@ __device__ __forceinline__ void fill_seg_cache(SegCache &c, const RunArgs &a, in
     if (lane < n) {
         c.seg[lane] = a.segs[sbeg + lane];
         c.inst[lane] = a.inst[c.seg[lane].inst];
+        c.bufs[lane] = inst_bufs(a, c.inst[lane], c.seg[lane].inst);
     }
     __syncwarp();
 }
@@ -967,7 +977,7 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
             const bool cached = (k - sbeg) < SEG_CACHE;
             const Seg sg = cached ? cache.seg[k - sbeg] : a.segs[k];
             const Inst &I = cached ? cache.inst[k - sbeg] : a.inst[sg.inst];
-            const Bufs B{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, a.store};
+            const Bufs B = cached ? cache.bufs[k - sbeg] : inst_bufs(a, I, sg.inst);
             bad |= S::seg(a, I, mp, B, nullptr, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
                           sg.mb0, sg.mb1,
                           s, step, lane);
@@ -984,7 +994,7 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
             for (int t = blockIdx.x * nwarps + warp; t < a.n_tiles; t += gridDim.x * nwarps) {
                 const int i = find_inst(t);
                 const Inst &I = a.inst[i];
-                bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+                bad |= S::tile(a, I, i, mp, t - I.tile_begin, s, step, lane);
             }
         }
     } else {
@@ -1005,7 +1015,7 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
                     if (lane == 0) tn = (int)atomicAdd(q, 1u);
                     const int i = find_inst(t);
                     const Inst &I = a.inst[i];
-                    bad |= S::tile(a, I, mp, t - I.tile_begin, s, step, lane);
+                    bad |= S::tile(a, I, i, mp, t - I.tile_begin, s, step, lane);
                     t = __shfl_sync(CG_FULL, tn, 0);
                 }
             }
