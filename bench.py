@@ -58,7 +58,7 @@ def parse():
                          "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), or on "
                          "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
                          "16 steps (adj)")
-    ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence"],
+    ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence", "orbit"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
 
@@ -362,6 +362,23 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     torch.cuda.synchronize()
     t_adj = e0.elapsed_time(e1) / 1e3
     plan.status()
+    # the same gradient keeping every stage input of the whole horizon in
+    # HBM (one segment: no checkpoint sweep, no recomputation)
+    import ctypes
+    from paper_1309_1720_gb300 import _lib
+    sz = ctypes.c_size_t()
+    _lib.check(_lib.lib().cg_adjoint_workspace_size(plan.handle, T, T, ctypes.byref(sz)))
+    plan.adjoint(z, lamT, T, checkpoint_every=T)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.adjoint(z, lamT, T, checkpoint_every=T)
+    e1.record()
+    torch.cuda.synchronize()
+    t_adj_all = e0.elapsed_time(e1) / 1e3
+    plan.status()
+    plan._ws = None
+    torch.cuda.empty_cache()
     g_plain = n * n * T / t_plain / 1e9
     rows["grad-512x512-5pt-rk4"] = {
         "gcups_plain": g_plain,
@@ -370,8 +387,12 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         "adjoint_gcups": n * n * T / t_adj / 1e9,
         "adjoint_seconds_T2000": t_adj,
         "adjoint_vs_plain": (n * n * T / t_adj / 1e9) / g_plain,
+        "adjoint_seconds_T2000_all_stages_stored": t_adj_all,
+        "adjoint_all_stages_workspace_gb": sz.value / 1e9,
+        "adjoint_all_stages_vs_plain": (n * n * T / t_adj_all / 1e9) / g_plain,
         "note": "tlm: 64 tangents x 200 steps (rate); adjoint: full T = 2000 with ceil(sqrt(T)) checkpoints "
-                "(forward + segment recompute + reverse sweep)"}
+                "(forward + segment recompute + reverse sweep), and with every stage input of the horizon "
+                "kept in HBM (forward with stores + reverse sweep)"}
     plan.close()
     return rows
 
@@ -458,6 +479,40 @@ def paper_experiments(which):
         print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": "fhn 5-point", "steps": 2000,
                           "fit": "t = a max(1, (N/N0)^2), a = median of N <= 64, b = a/N0^2 = median t/N^2 "
                                  "for N >= 2048", "results": res}), flush=True)
+    if which in ("all", "orbit"):
+        # Sect. 1's use: a periodic orbit by Newton-Krylov.  A FitzHugh-Nagumo
+        # pulse travelling round a periodic ring (512 x 2 cells, dx = 0.5)
+        from paper_1309_1720_gb300.newton import periodic_orbit
+        nx, ny, dt = 512, 2, 0.05
+        base = api.Problem(model=api.FHN, nx=nx, ny=ny, dx=0.5, bc=api.PERIODIC, scheme=api.RK4, dt=dt)
+        z = np.empty((2, ny, nx))
+        z[0], z[1] = I.FHN_U_REST, I.FHN_V_REST
+        z[0, :, 10:20] = 1.0
+        z[1, :, 0:10] = 0.6
+        z[1, :, -30:] = 0.6
+        plan = Plan(base)
+        zd = plan.run(torch.from_numpy(z).cuda(), 6000)
+
+        def front(u):
+            k = int(np.argmax(u))
+            for j in range(u.size):
+                a0, b0 = u[(k + j) % u.size], u[(k + j + 1) % u.size]
+                if a0 >= 0.0 > b0:
+                    return k + j + a0 / (a0 - b0)
+            return float(k)
+        x0 = front(zd[0, 0].cpu().numpy())
+        zd = plan.run(zd, 2000)
+        x1 = front(zd[0, 0].cpu().numpy())
+        T0 = nx / (((x1 - x0) % nx) / (2000 * dt))
+        n_steps = int(round(T0 / dt))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, T, hist = periodic_orbit(base, zd, T0, n_steps, tol=1e-12)
+        torch.cuda.synchronize()
+        print(json.dumps({"experiment": "periodic orbit by Newton-Krylov (Sect. 1)",
+                          "system": "FitzHugh-Nagumo pulse on a periodic 512 x 2 ring, dx = 0.5, RK4, %d steps "
+                                    "per period" % n_steps,
+                          "T0": T0, "T": T, "seconds": time.perf_counter() - t, "newton": hist}), flush=True)
     if which in ("all", "convergence", "efficiency"):
         conv = {}
         for mname, m in models.items():
