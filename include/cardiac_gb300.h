@@ -120,7 +120,7 @@ typedef struct cg_problem {
 typedef struct cg_tuning {
     int32_t cells_x;       /* cells per lane along x: 1 or 2 (warp tile width 32 or 64) */
     int32_t rows;          /* rows per warp tile, >= 1 */
-    int32_t threads;       /* threads per block: 128, 256 or 512 */
+    int32_t threads;       /* threads per block: a multiple of 32 from 64 to 512 */
     int32_t blocks_per_sm; /* persistent blocks per SM, >= 1 (capped by occupancy) */
     int32_t schedule;      /* 0: static (equal cells per block, equal strip-rows per warp,
                               computed at plan creation); 1: atomic tile queue per stage

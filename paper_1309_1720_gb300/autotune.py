@@ -41,6 +41,11 @@ DEFAULT_CANDIDATES: List[Dict] = [
     dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=1, rows=8),
     dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=4),
     dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0, sync="per_stage"),
+    # fewer, longer warp shares: the 9-point window's start-up rows are
+    # amortised over more rows, at lower occupancy
+    dict(cells_x=2, threads=256, blocks_per_sm=1, schedule=0),
+    dict(cells_x=1, threads=256, blocks_per_sm=1, schedule=0),
+    dict(cells_x=2, threads=384, blocks_per_sm=1, schedule=0),
 ]
 
 

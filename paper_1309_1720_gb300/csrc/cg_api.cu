@@ -478,10 +478,10 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         return fail(CG_EINVAL, "tuning.schedule must be 0 (static) or 1 (queue)");
     }
     if ((P->cx != 1 && P->cx != 2) || P->rows < 1 || P->rows > 4096 ||
-        (P->threads != 128 && P->threads != 256 && P->threads != 512) || P->bpsm < 1 || P->bpsm > 8) {
+        P->threads < 64 || P->threads > 512 || (P->threads % 32) != 0 || P->bpsm < 1 || P->bpsm > 8) {
         delete P;
-        return fail(CG_EINVAL, "tuning out of range (cells_x 1|2, rows >= 1, threads 128|256|512, "
-                               "blocks_per_sm 1..8)");
+        return fail(CG_EINVAL, "tuning out of range (cells_x 1|2, rows >= 1, threads a multiple of 32 in "
+                               "[64, 512], blocks_per_sm 1..8)");
     }
     P->kernel = lookup_kernel(P->kmodel, P->stencil, P->scheme, P->cx);
     if (!P->kernel) {
