@@ -16,10 +16,11 @@
 // work (index arithmetic, clamps of the smoothed steps, NaN checks) is done
 // with integer instructions.
 //
+// Work assignment: a static schedule computed on the host (equal cells per
+// block, equal strip-rows per warp) or an atomic tile queue per stage.
 // Launch modes: persistent (one cooperative launch runs all stages of all
-// steps; tiles are handed out by an atomic queue per stage and stages are
-// separated by a bounded grid barrier) or one launch per stage (static tile
-// assignment, no waiting).
+// steps, separated by a bounded grid barrier or by bounded waits on the
+// blocks that own a block's halo) or one launch per stage (no waiting).
 #pragma once
 
 #include "cg_fastmath.cuh"
@@ -56,14 +57,6 @@ __device__ __forceinline__ double clamp01_int(double t)
     b = b < 0 ? 0 : b;
     b = b > 0x3FF0000000000000ll ? 0x3FF0000000000000ll : b;
     return __longlong_as_double(b);
-}
-
-// Smoothed step H_k(u - theta) of Sect. 2 with t = k (u - theta) + 1/2
-// clamped to [0, 1]; H = t^2 (3 - 2 t).  c = 1/2 - k theta.
-__device__ __forceinline__ double smooth_step(double u, double k, double c)
-{
-    double t = clamp01_int(fma(k, u, c));
-    return (t * t) * fma(-2.0, t, 3.0);
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)

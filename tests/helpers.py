@@ -13,7 +13,6 @@ def oracle_problem(p):
     """Oracle record for a paper_1309_1720_gb300.Problem."""
     from paper_1309_1720_gb300 import api
     c = p.to_c()
-    nv = api.n_fields(p.model) if False else O.n_fields(_MODEL[p.model])
     return O.problem(_MODEL[p.model], nx=p.nx, ny=p.ny, dx=c.dx, dy=c.dy,
                      Dxx=[c.Dxx[i] for i in range(4)], Dyy=[c.Dyy[i] for i in range(4)],
                      stencil=p.stencil, alpha_d=p.alpha_d, bc=p.bc, scheme=p.scheme, dt=p.dt,

@@ -218,7 +218,7 @@ def test_bocf_saturated_limits():
     # u = 0.2
     u = 0.2
     f = O.pointwise(p, [u, v, w, s])
-    exp = [-(1 / tau_so(u) - w * s / tsi), -v / tv2m if False else (0 - v) / tv2m,
+    exp = [-(1 / tau_so(u) - w * s / tsi), (0 - v) / tv2m,      # v_inf = 0 once the v- switch is on
            -w / twp, (sinf(u) - s) / ts2]
     assert np.allclose(f, exp, rtol=1e-14, atol=1e-16)
     # u = 1.0
