@@ -29,7 +29,12 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
+    # --fmad=false: no implicit contraction of a*b + c.  Every FMA in the
+    # kernels is written out with fma(), so results are a function of the
+    # source alone, identical across template instantiations (launch shapes,
+    # the shortcut and general paths of the four-field model, the plain and
+    # the tangent-linear primal).
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "--fmad=false",
                    "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
                    "-I", INCLUDE, "-I", CSRC] + list(extra)
 

@@ -42,13 +42,14 @@ struct Adjoint {
     using SP = Stepper<M, ST, NS, CX>;
     static constexpr int NV = MD::NV, ND = MD::ND, NJ = MD::NJ;
 
-    // Load one row of a kbar plane scaled by W^-1 (MIRROR).
+    // Load one row of a kbar plane scaled by W^-1 (MIRROR; BND segments only).
+    template <bool BND>
     __device__ static inline void load_scaled(const double *plane, int nx, int ny, int yrow, const int (&cx)[CX],
                                               int hx, bool vec, bool want_halo, bool mirror, bool xedge,
                                               const double (&fx)[CX], double fh, double (&v)[CX], double &h)
     {
         SP::load_row(plane, nx, yrow, cx, hx, vec, want_halo, v, h);
-        if (mirror) {
+        if (BND && mirror) {
             if (yrow == 0 || yrow == ny - 1) {
 #pragma unroll
                 for (int c = 0; c < CX; ++c) v[c] *= 2.0;
@@ -62,6 +63,16 @@ struct Adjoint {
         }
     }
 
+    // A segment is a BND segment when it may load or own a cell of a
+    // boundary row or column (mirror ghosts only): only those carry the
+    // W^-1 / W scaling, so the interior's code has none of it.
+    __device__ __forceinline__ static bool bnd_segment(const RunArgs &a, const Inst &I, const Seg &sg)
+    {
+        return a.bc == CG_BC_MIRROR && (sg.x0 <= 1 || sg.x0 + 32 * CX >= I.nx - 1 || sg.y0 <= 1 ||
+                                        sg.y1 >= I.ny - 2);
+    }
+
+    template <bool BND>
     __device__ __forceinline__ static uint32_t seg(const RunArgs &a, const AdjArgs &b, const Inst &I,
                                                    const double *mp, const Seg &sg, int64_t k, int s, int64_t r,
                                                    int lane, double (&dd)[ND > 0 ? ND : 1])
@@ -114,7 +125,7 @@ struct Adjoint {
         }
         const double fh = (hx == 0 || hx == nx - 1) ? 2.0 : 1.0;
         if (want_halo && fh != 1.0) edge_lane = true;
-        const bool xedge = mirror && __any_sync(CG_FULL, edge_lane);
+        const bool xedge = BND && mirror && __any_sync(CG_FULL, edge_lane);
 
         double wx[ND], wy[ND], wd[ND], wcf[ND];
 #pragma unroll
@@ -131,9 +142,9 @@ struct Adjoint {
 #pragma unroll
         for (int f = 0; f < ND; ++f) {
             hlo[f] = hmid[f] = hhi[f] = 0.0;
-            load_scaled(Kin + f * plane, nx, ny, map_idx(sg.y0 - 1, ny, bc), cx, hx, vk, want_halo, mirror, xedge,
+            load_scaled<BND>(Kin + f * plane, nx, ny, map_idx(sg.y0 - 1, ny, bc), cx, hx, vk, want_halo, mirror, xedge,
                         fx, fh, lo[f], hlo[f]);
-            load_scaled(Kin + f * plane, nx, ny, sg.y0, cx, hx, vk, want_halo, mirror, xedge, fx, fh, mid[f],
+            load_scaled<BND>(Kin + f * plane, nx, ny, sg.y0, cx, hx, vk, want_halo, mirror, xedge, fx, fh, mid[f],
                         hmid[f]);
         }
 
@@ -142,10 +153,10 @@ struct Adjoint {
             const int yn = map_idx(y + 1, ny, bc);
 #pragma unroll
             for (int f = 0; f < ND; ++f)
-                load_scaled(Kin + f * plane, nx, ny, yn, cx, hx, vk, want_halo, mirror, xedge, fx, fh, hi[f],
+                load_scaled<BND>(Kin + f * plane, nx, ny, yn, cx, hx, vk, want_halo, mirror, xedge, fx, fh, hi[f],
                             hhi[f]);
             const unsigned own = (y == sg.mrow_a) ? own_a : ((y == sg.mrow_b) ? own_b : in_grid);
-            const bool yedge = mirror && (y == 0 || y == ny - 1);
+            const bool yedge = BND && mirror && (y == 0 || y == ny - 1);
             const bool bnd = yedge || xedge;      // warp-uniform: some cell of this row may sit on the boundary
             double wcell[CX];
 #pragma unroll
@@ -284,7 +295,10 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
         const int s = NS - 1 - (int)(g % NS);
         for (int q = sbeg; q < send; ++q) {
             const Seg sg = (q - sbeg) < SEG_CACHE ? cache.seg[q - sbeg] : a.segs[q];
-            bad |= AD::seg(a, b, I, mp, sg, k, s, b.r0 + g, lane, dd);
+            if (AD::bnd_segment(a, I, sg))
+                bad |= AD::template seg<true>(a, b, I, mp, sg, k, s, b.r0 + g, lane, dd);
+            else
+                bad |= AD::template seg<false>(a, b, I, mp, sg, k, s, b.r0 + g, lane, dd);
         }
     };
 

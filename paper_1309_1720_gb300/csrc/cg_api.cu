@@ -545,6 +545,8 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
 
     // device table and persistent grid
     cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess && P->model == CG_BOCF)
+        e = cgk::bocf_rcp_constants(P->mp[cgk::BP_TS1], P->mp[cgk::BD_DTS], &P->mp[cgk::BD_RS0]);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, P->kernel, P->threads, 0);

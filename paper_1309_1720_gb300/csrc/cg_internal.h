@@ -10,7 +10,7 @@
 namespace cgk {
 
 constexpr int MAXF = 4;     // fields per cell (BOCF: u, v, w, s)
-constexpr int NMP = 56;     // model constants shared by all instances of a plan
+constexpr int NMP = 64;     // model constants shared by all instances of a plan
 constexpr int EXP_TAB = 256; // entries 2^(j/256) of the exponential's table (cg_fastmath.cuh)
 
 // One grid instance, resident in a plan-owned device table.  Coefficients
@@ -103,6 +103,11 @@ const void *tlm_kernel_diff(int stencil, int scheme, int cx);
 const void *adj_kernel_fhn(int stencil, int scheme, int cx);
 const void *adj_kernel_bocf(int stencil, int scheme, int cx);
 const void *adj_kernel_diff(int stencil, int scheme, int cx);
+
+// Host: the four-field model's s-gate rates 1/ts1 and 1/(ts1 + dts) as the
+// kernels' own reciprocal computes them (out[0], out[1]); runs one tiny
+// kernel on the current device and waits for it.
+cudaError_t bocf_rcp_constants(double ts1, double dts, double *out);
 
 // Host: fill tab[j] = 2^(j / n), j = 0..n-1, each rounded once to double
 // from extended precision (the exponential's table).

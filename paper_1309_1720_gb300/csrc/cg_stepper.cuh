@@ -272,6 +272,8 @@ enum {
     BD_ASOH,           // 1/2 - kso uso / 3
     BD_KSH,            // ks / 3
     BD_ASH,            // 1/2 - ks us / 3
+    BD_RS0,            // 1/ts1 by fast_rcp on the device (the s-gate rate where H_w = 0)
+    BD_RS1,            // 1/(ts1 + (ts2 - ts1)) likewise (H_w = 1)
     BD_N
 };
 
@@ -309,6 +311,32 @@ template <bool TH> struct BocfModel {
             return sigmoid(fma(mp[IK], u, mp[IA]), tab);
         }
     }
+    // 1 / (tau1 + dtau (1 + tanh(kk (u - cc)))/2), the rates of the
+    // u-dependent time constants tau_w^- and tau_so.  In the sigmoid form
+    // s = 1/(1 + e) (a >= 0) or e/(1 + e) (a < 0), e = e^-|a|, so
+    // 1/(tau1 + dtau s) = (1 + e)/(tau1 (1 + e) + dtau sel), sel = 1 or e:
+    // one reciprocal instead of two.  With DS, ds = s (1 - s) as in
+    // half_tanh.
+    template <int IA, int IK, int IHA, int IHK, bool DS>
+    __device__ __forceinline__ static double rcp_tau(const double *mp, double u, const double *tab, double tau1,
+                                                     double dtau, double &ds)
+    {
+        if constexpr (TH) {
+            const double t = clamp01_int(fma(mp[IHK], u, mp[IHA]));
+            if constexpr (DS) ds = t * (1.0 - t);
+            return fast_rcp(fma(dtau, (t * t) * fma(-2.0, t, 3.0), tau1));
+        } else {
+            const double a = fma(mp[IK], u, mp[IA]);
+            const double e = exp_neg(a, tab);
+            const double ope = 1.0 + e;
+            const double sel = (__double_as_longlong(a) >= 0) ? dtau : dtau * e;
+            if constexpr (DS) {
+                const double r1 = fast_rcp(ope);
+                ds = (e * r1) * r1;
+            }
+            return ope * fast_rcp(fma(tau1, ope, sel));
+        }
+    }
 #define CG_SW BD_AW2, BD_KW2, BD_AWH, BD_KWH
 #define CG_SSO BD_ASO2, BD_KSO2, BD_ASOH, BD_KSOH
 #define CG_SS BD_AS2, BD_KS2, BD_ASH, BD_KSH
@@ -340,12 +368,12 @@ template <bool TH> struct BocfModel {
                 const double Ho = (to * to) * fma(-2.0, to, 3.0);
                 const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
                 const double v_inf = 1.0 - Hvm;
-                const double sw = half_tanh<CG_SW>(mp, u, c.tab);
-                const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
+                double unused;
+                const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], unused);
                 const double q = fma(-u, mp[BD_IWINF], 1.0);
                 const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
                 const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-                const double r_s = fast_rcp(mp[BP_TS1]);
+                const double r_s = mp[BD_RS0];
                 const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
                 const double uo = u - mp[BP_UO];
                 t[0] = fma(c.wc_u, u, -(uo * r_o));
@@ -357,8 +385,9 @@ template <bool TH> struct BocfModel {
             if (__all_sync(CG_FULL, bv == ONE && bw == ONE && __double_as_longlong(tvm) == ONE &&
                                         __double_as_longlong(to) == ONE)) {
                 // excited tissue: every switch is 1
-                const double r_so = fast_rcp(fma(mp[BD_DTSO], half_tanh<CG_SSO>(mp, u, c.tab), mp[BP_TSO1]));
-                const double r_s = fast_rcp(fma(1.0, mp[BD_DTS], mp[BP_TS1]));
+                double unused;
+                const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], unused);
+                const double r_s = mp[BD_RS1];
                 const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
                 const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u;
                 const double J_fi = -v * (ua * ub) * mp[BD_IFI];
@@ -377,14 +406,12 @@ template <bool TH> struct BocfModel {
         const double tau_vm = fma(Hvm, mp[BD_DTV], mp[BP_TV1M]);
         const double r_vm = fast_rcp(tau_vm);
         const double v_inf = 1.0 - Hvm;
-        double dsw, dsso, dss;
-        const double sw = half_tanh<CG_SW>(mp, u, c.tab, dsw);
-        const double r_wm = fast_rcp(fma(mp[BD_DTW], sw, mp[BP_TW1M]));
+        double dsw = 0.0, dsso = 0.0, dss;
+        const double r_wm = rcp_tau<CG_SW, JAC>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], dsw);
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
         const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-        const double sso = half_tanh<CG_SSO>(mp, u, c.tab, dsso);
-        const double r_so = fast_rcp(fma(mp[BD_DTSO], sso, mp[BP_TSO1]));
+        const double r_so = rcp_tau<CG_SSO, JAC>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], dsso);
         const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
         const double s_inf = half_tanh<CG_SS>(mp, u, c.tab, dss);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
@@ -472,11 +499,12 @@ template <bool TH> struct BocfModel {
         const double Ho = (to * to) * fma(-2.0, to, 3.0);
         const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
         const double v_inf = 1.0 - Hvm;
-        const double r_wm = fast_rcp(fma(mp[BD_DTW], half_tanh<CG_SW>(mp, u, c.tab), mp[BP_TW1M]));
+        double unused;
+        const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], unused);
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
         const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-        const double r_so = fast_rcp(fma(mp[BD_DTSO], half_tanh<CG_SSO>(mp, u, c.tab), mp[BP_TSO1]));
+        const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], unused);
         const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
         const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
