@@ -103,3 +103,21 @@ def test_batch_run_separate_buffers(cuda_ok, scheme):
         plan.status()
         for g, r in zip(got, ref):
             assert np.array_equal(g.cpu().numpy(), r), n
+
+
+@pytest.mark.parametrize("tuning", [None, dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=1, rows=8)])
+def test_batch_full_size_against_oracle(cuda_ok, tuning):
+    """The full 256-instance workload in one launch (default shape and the
+    tile-queue shape the autotuner picks for the bench), 20 RK4 steps: the
+    smallest, the largest and two other instances against the oracle."""
+    import torch
+    from helpers import field_rel_err, oracle_run
+    from paper_1309_1720_gb300 import Plan
+    sizes, states, dus = I.batch_workload(n_inst=256, seed=1)
+    probs = _problems(sizes, dus)
+    bp = Plan(probs, tuning=tuning)
+    parts = bp.unpack(bp.run(bp.pack(states), 20))
+    bp.status()
+    order = sorted(range(len(sizes)), key=lambda i: int(sizes[i]))
+    for i in (order[0], order[-1], 37, 200):
+        assert field_rel_err(parts[i].cpu().numpy(), oracle_run(probs[i], states[i], 20)) <= 1e-12, i

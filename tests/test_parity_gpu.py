@@ -105,14 +105,17 @@ def test_c2_first_100_steps(cuda_ok):
     assert field_rel_err(g, o) <= TOL
 
 
-def test_c3_sampled_windows(cuda_ok):
-    """2048^2 four-field model, anisotropic 9-point, RK4, 10 steps: the
-    oracle recomputes windows whose margin (4 cells per step) covers the
-    domain of dependence, so the window's interior is exact."""
+@pytest.mark.parametrize("tuning", [None, dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=4)])
+def test_c3_sampled_windows(cuda_ok, tuning):
+    """2048^2 four-field model, anisotropic 9-point, RK4, 10 steps, with the
+    default launch shape and with the tile-queue shape the autotuner picks
+    for the bench: the oracle recomputes windows whose margin (4 cells per
+    step) covers the domain of dependence, so the window's interior is
+    exact."""
     n, steps = 2048, 10
     p = _bocf(n, n)
     z0 = I.bocf_spiral_cores(n, n, seed=0)
-    g = gpu_run(p, z0, steps)
+    g = gpu_run(p, z0, steps, tuning=tuning)
     margin = 4 * steps + 2
     for (y0, x0) in [(0, 0), (0, 1000), (1000, 0), (900, 1300), (2048 - 24, 2048 - 24), (0, 2048 - 24)]:
         ys, xs = max(0, y0 - margin), max(0, x0 - margin)
