@@ -56,23 +56,38 @@ __global__ void k_axpby(double a, const double *x, double b, double *y, int64_t 
 
 }  // namespace
 
+namespace {
+
+// Status with a message for cg_last_error().
+cg_status err(cg_status st, const char *msg)
+{
+    return cgk::set_last_error(st, msg);
+}
+
+cg_status cuda_err(cudaError_t e)
+{
+    return e == cudaSuccess ? CG_OK : cgk::set_last_error(CG_ECUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
 CG_API cg_status cg_dot(const double *x, const double *y, int64_t n, double *result, void *workspace, void *stream)
 {
-    if (!x || !y || !result || !workspace || n < 0) return CG_EINVAL;
+    if (!x || !y || !result || !workspace || n < 0) return err(CG_EINVAL, "cg_dot: NULL buffer or n < 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     double *part = reinterpret_cast<double *>(workspace);
     k_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(x, y, n, part);
     k_dot_final<<<1, 32, 0, s>>>(part, result);
-    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+    return cuda_err(cudaGetLastError());
 }
 
 CG_API cg_status cg_axpby(double a, const double *x, double b, double *y, int64_t n, void *stream)
 {
-    if (!x || !y || n < 0) return CG_EINVAL;
+    if (!x || !y || n < 0) return err(CG_EINVAL, "cg_axpby: NULL buffer or n < 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t blocks = std::min<int64_t>(4096, (n + 255) / 256 + 1);
     k_axpby<<<(unsigned)blocks, 256, 0, s>>>(a, x, b, y, n);
-    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+    return cuda_err(cudaGetLastError());
 }
 
 namespace {
@@ -86,13 +101,13 @@ struct Dev {
         k_dot_final<<<1, 32, 0, s>>>(dpart, dres);
         cudaError_t e = cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        return e == cudaSuccess ? CG_OK : CG_ECUDA;
+        return cuda_err(e);
     }
     cg_status axpby(double a, const double *x, double b, double *y, int64_t n)
     {
         const int64_t blocks = std::min<int64_t>(4096, (n + 255) / 256 + 1);
         k_axpby<<<(unsigned)blocks, 256, 0, s>>>(a, x, b, y, n);
-        return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+        return cuda_err(cudaGetLastError());
     }
 };
 
@@ -100,11 +115,11 @@ struct Dev {
 
 CG_API cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t *bytes)
 {
-    if (!plan || !bytes || restart < 1) return CG_EINVAL;
+    if (!plan || !bytes || restart < 1) return err(CG_EINVAL, "cg_newton_workspace_size: bad argument");
     int64_t off[2];
     cg_status st = cg_batch_offsets(plan, off);
     if (st != CG_OK) return st;
-    if (cg_plan_n_instances(plan) != 1) return CG_EUNSUPPORTED;
+    if (cg_plan_n_instances(plan) != 1) return err(CG_EUNSUPPORTED, "Newton steps need a single-instance plan");
     size_t tws = 0;
     st = cg_tlm_workspace_size(plan, 1, &tws);
     if (st != CG_OK) return st;
@@ -119,9 +134,9 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
                                       int32_t *n_iter, void *workspace, void *stream)
 {
     if (!plan || !z0 || !dz || !workspace || period_steps < 1 || restart < 1 || max_restarts < 1 || !(rtol > 0))
-        return CG_EINVAL;
+        return err(CG_EINVAL, "cg_newton_gmres_step: bad argument");
     int64_t off[2];
-    if (cg_plan_n_instances(plan) != 1) return CG_EUNSUPPORTED;
+    if (cg_plan_n_instances(plan) != 1) return err(CG_EUNSUPPORTED, "Newton steps need a single-instance plan");
     cg_status st = cg_batch_offsets(plan, off);
     if (st != CG_OK) return st;
     const int64_t n = off[1];
@@ -145,10 +160,10 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
     st = cg_run(plan, z0, phi, period_steps, base, stream);
     if (st != CG_OK) return st;
     cudaError_t e = cudaMemcpyAsync(w, z0, sizeof(double) * n, cudaMemcpyDeviceToDevice, d.s);
-    if (e != cudaSuccess) return CG_ECUDA;
+    if (e != cudaSuccess) return cuda_err(e);
     if ((st = d.axpby(-1.0, phi, 1.0, w, n)) != CG_OK) return st;          // w = z0 - Phi
     e = cudaMemsetAsync(dz, 0, sizeof(double) * n, d.s);
-    if (e != cudaSuccess) return CG_ECUDA;
+    if (e != cudaSuccess) return cuda_err(e);
     double bnorm2 = 0;
     if ((st = d.dot(w, w, n, &bnorm2)) != CG_OK) return st;
     const double bnorm = std::sqrt(bnorm2);
@@ -160,13 +175,13 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
     }
     // r lives in phi: r = b - A dz (dz = 0 at start)
     e = cudaMemcpyAsync(phi, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, d.s);
-    if (e != cudaSuccess) return CG_ECUDA;
+    if (e != cudaSuccess) return cuda_err(e);
     double rnorm = bnorm;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     for (int cycle = 0; cycle < max_restarts && rnorm > rtol * bnorm; ++cycle) {
         // V0 = r / |r|
         e = cudaMemcpyAsync(V, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, d.s);
-        if (e != cudaSuccess) return CG_ECUDA;
+        if (e != cudaSuccess) return cuda_err(e);
         if ((st = d.axpby(0.0, V, 1.0 / rnorm, V, n)) != CG_OK) return st;
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = rnorm;
@@ -232,6 +247,5 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
         rnorm = std::sqrt(r2);
     }
     if (n_iter) *n_iter = iters;
-    e = cudaStreamSynchronize(d.s);
-    return e == cudaSuccess ? CG_OK : CG_ECUDA;
+    return cuda_err(cudaStreamSynchronize(d.s));
 }
