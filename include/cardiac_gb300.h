@@ -125,7 +125,13 @@ typedef struct cg_tuning {
     int32_t schedule;      /* 0: static (equal cells per block, equal strip-rows per warp,
                               computed at plan creation); 1: atomic tile queue per stage
                               (tiles of 32*cells_x columns by `rows` rows, largest
-                              instances first) */
+                              instances first); 2: temporal blocking of cg_run for small
+                              grids: each block advances a tile and its halo through `rows`
+                              steps (default 2) in shared memory per grid barrier, with
+                              `threads` per block (default 256); one instance, MIRROR or
+                              CLAMP ghosts, EULER/HEUN/RK4 only (else CG_EUNSUPPORTED), the
+                              same results bit for bit; the plan's other entry points use
+                              the default launch shape */
 } cg_tuning;
 
 typedef struct cg_plan_s *cg_plan;

@@ -7,8 +7,9 @@ knobs:
 
 * ``cells_x``: cells per lane along x (tile width 32 or 64 columns);
 * ``threads``, ``blocks_per_sm``: warps per SM of the persistent grid;
-* ``schedule``: static balanced segments, or the atomic tile queue with
-  ``rows`` rows per tile;
+* ``schedule``: static balanced segments, the atomic tile queue with
+  ``rows`` rows per tile, or temporal blocking (2) with ``rows`` steps per
+  grid barrier;
 * synchronisation depth between stages: a grid-wide barrier (default),
   neighbour-only waits, or one kernel launch per RK stage (the shallowest
   fusion: one stage per pass instead of every stage of the run in one pass).
@@ -46,6 +47,13 @@ DEFAULT_CANDIDATES: List[Dict] = [
     dict(cells_x=2, threads=256, blocks_per_sm=1, schedule=0),
     dict(cells_x=1, threads=256, blocks_per_sm=1, schedule=0),
     dict(cells_x=2, threads=384, blocks_per_sm=1, schedule=0),
+    # temporal blocking (small grids): k steps per grid barrier in shared
+    # memory; plan creation fails, and the candidate is skipped, where a
+    # tile and its halo do not fit
+    dict(schedule=2, rows=1, threads=256),
+    dict(schedule=2, rows=2, threads=256),
+    dict(schedule=2, rows=4, threads=256),
+    dict(schedule=2, rows=8, threads=256),
 ]
 
 

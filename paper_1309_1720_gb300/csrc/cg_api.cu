@@ -14,6 +14,7 @@
 #include "cg_internal.h"
 #include "cg_tlm.cuh"
 #include "cg_adjoint.cuh"
+#include "cg_tblock.cuh"
 
 #define CG_API extern "C" __attribute__((visibility("default")))
 
@@ -134,6 +135,11 @@ struct cg_plan_s {
     double cacc[4] = {}, cy[4] = {};
     uint64_t timeout_ns = 0;
     const void *kernel = nullptr;
+    // temporal blocking of cg_run (tuning.schedule = 2): steps per pass (0 =
+    // off), tile size, tiles along x, blocks, threads, window cells, kernel
+    int32_t tb_k = 0, tb_tx = 0, tb_ty = 0, tb_tiles_x = 0, tb_blocks = 0, tb_threads = 0, tb_wmax = 0;
+    size_t tb_smem = 0;
+    const void *tb_kernel = nullptr;
     int nblocks = 0;
     double dxx[4] = {};              // Dxx of the first instance (gradient normalisation)
     std::vector<int2> deps;          // halo owners of each block (neighbour sync)
@@ -152,6 +158,17 @@ void exp_table(double *tab, int n)
 }  // namespace cgk
 
 namespace {
+
+const void *lookup_tb_kernel(int kmodel, int stencil, int scheme)
+{
+    switch (kmodel) {
+    case CG_FHN: return cgk::tb_kernel_fhn(stencil, scheme);
+    case CG_BOCF: return cgk::tb_kernel_bocf(stencil, scheme);
+    case CG_DIFFUSION: return cgk::tb_kernel_diff(stencil, scheme);
+    case cgk::MODEL_BOCFH: return cgk::tb_kernel_bocfh(stencil, scheme);
+    default: return nullptr;
+    }
+}
 
 const void *lookup_kernel(int kmodel, int stencil, int scheme, int cx)
 {
@@ -428,6 +445,62 @@ void halo_dependencies(const std::vector<int32_t> &nxs, const std::vector<int32_
     }
 }
 
+// Tiles of the temporally blocked kernel: about one tile per SM, square
+// unless the grid is thinner than that, every tile resident at once (the
+// launch is cooperative), the window (tile plus k n_s halo cells, clipped
+// at the ghost layer) in shared memory.
+cg_status tb_setup(cg_plan_s *P, const cg_problem &p)
+{
+    P->tb_kernel = lookup_tb_kernel(P->kmodel, P->stencil, P->scheme);
+    if (!P->tb_kernel) return fail(CG_EUNSUPPORTED, "no temporally blocked kernel for this problem");
+    const int nx = (int)p.nx, ny = (int)p.ny, H = P->tb_k * P->ns;
+    int dev_smem = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    if (e != cudaSuccess) return cuda_fail(e, "device attribute");
+    const int64_t cells = (int64_t)nx * ny;
+    const int64_t per = (cells + P->num_sms - 1) / P->num_sms;
+    int ty = (int)std::ceil(std::sqrt((double)per)), tx = ty;
+    if (ty > ny) {
+        ty = ny;
+        tx = (int)((per + ny - 1) / ny);
+    }
+    tx = std::max(1, std::min(tx, nx));
+    for (int attempt = 0; attempt < 4096; ++attempt) {
+        const int tiles_x = (nx + tx - 1) / tx, tiles_y = (ny + ty - 1) / ty;
+        int wmax = 0;
+        for (int by = 0; by < tiles_y; ++by)
+            for (int bx = 0; bx < tiles_x; ++bx) {
+                int w0, w1, h0, h1;
+                cgk::tb_window(bx * tx, std::min(bx * tx + tx, nx), nx, H, w0, w1);
+                cgk::tb_window(by * ty, std::min(by * ty + ty, ny), ny, H, h0, h1);
+                wmax = std::max(wmax, (w1 - w0) * (h1 - h0));
+            }
+        const size_t smem = cgk::tb_smem_bytes(P->nv, P->ns, wmax);
+        if (smem + sizeof(Inst) > (size_t)dev_smem)
+            return fail(CG_EUNSUPPORTED, "temporal blocking: a tile and its halo (%d steps) need %zu bytes of "
+                                         "shared memory, the device has %d", P->tb_k, smem, dev_smem);
+        e = cudaFuncSetAttribute(P->tb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "shared memory attribute");
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, P->tb_kernel, P->tb_threads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        if (occ >= 1 && tiles_x * tiles_y <= occ * P->num_sms) {
+            P->tb_tx = tx;
+            P->tb_ty = ty;
+            P->tb_tiles_x = tiles_x;
+            P->tb_blocks = tiles_x * tiles_y;
+            P->tb_wmax = wmax;
+            P->tb_smem = smem;
+            return CG_OK;
+        }
+        // too many tiles to be resident together: make them larger
+        if (tx < nx && (tx <= ty || ty >= ny)) ++tx;
+        else if (ty < ny) ++ty;
+        else break;
+    }
+    return fail(CG_EUNSUPPORTED, "temporal blocking: no tile size fits this device");
+}
+
 cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tune, cg_plan *out)
 {
     if (!out) return fail(CG_EINVAL, "out is NULL");
@@ -466,7 +539,22 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     P->threads = 512;
     P->bpsm = 1;
     P->sched = cgk::SCHED_STATIC;
-    if (tune) {
+    if (tune && tune->schedule == cgk::SCHED_TBLOCK) {
+        // temporal blocking of cg_run; the plan's other kernels keep the
+        // default launch shape
+        P->tb_k = tune->rows ? tune->rows : 2;
+        P->tb_threads = tune->threads ? tune->threads : 256;
+        if (n_inst != 1 || p0.bc == CG_BC_PERIODIC || gate_scheme(p0.scheme)) {
+            delete P;
+            return fail(CG_EUNSUPPORTED, "temporal blocking needs one instance, mirror or clamp ghosts and an "
+                                         "explicit Euler, Heun or RK4 scheme");
+        }
+        if (P->tb_k < 1 || P->tb_k > 64 || P->tb_threads < 64 || P->tb_threads > 512 || (P->tb_threads % 32)) {
+            delete P;
+            return fail(CG_EINVAL, "temporal blocking: rows (steps per pass) in [1, 64], threads a multiple of "
+                                   "32 in [64, 512]");
+        }
+    } else if (tune) {
         if (tune->cells_x) P->cx = tune->cells_x;
         if (tune->rows) P->rows = tune->rows;
         if (tune->threads) P->threads = tune->threads;
@@ -475,7 +563,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     }
     if (P->sched != cgk::SCHED_STATIC && P->sched != cgk::SCHED_QUEUE) {
         delete P;
-        return fail(CG_EINVAL, "tuning.schedule must be 0 (static) or 1 (queue)");
+        return fail(CG_EINVAL, "tuning.schedule must be 0 (static), 1 (queue) or 2 (temporal blocking)");
     }
     if ((P->cx != 1 && P->cx != 2) || P->rows < 1 || P->rows > 4096 ||
         P->threads < 64 || P->threads > 512 || (P->threads % 32) != 0 || P->bpsm < 1 || P->bpsm > 8) {
@@ -563,6 +651,13 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
                         P->bc != CG_BC_PERIODIC &&
                         (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
+    }
+    if (e == cudaSuccess && P->tb_k > 0) {
+        const cg_status st = tb_setup(P, probs[0]);
+        if (st != CG_OK) {
+            delete P;
+            return st;
+        }
     }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_deps, sizeof(int2) * std::max<size_t>(1, P->deps.size()));
     if (e == cudaSuccess && !P->deps.empty())
@@ -830,6 +925,46 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
     const int64_t G = n_steps * plan->ns;
     void *args[] = {&a};
 
+    if (plan->tb_k > 0 && !tab) {
+        // temporally blocked: one cooperative launch, one grid barrier per
+        // tb_k steps (cg_tblock.cuh)
+        cgk::TbArgs t;
+        std::memset(&t, 0, sizeof t);
+        t.tx = plan->tb_tx;
+        t.ty = plan->tb_ty;
+        t.tiles_x = plan->tb_tiles_x;
+        t.k = plan->tb_k;
+        t.wmax = plan->tb_wmax;
+        t.alias = any_alias ? 1 : 0;
+        t.n_steps = n_steps;
+        t.zscr = a.ws + plan->inst[0].ws_off;
+        a.persistent = 1;
+        a.nblocks_expect = (uint32_t)plan->tb_blocks;
+        a.stuck_barrier = (plan->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
+        e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(barrier)");
+        void *targs[] = {&a, &t};
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3(plan->tb_blocks);
+        cfg.blockDim = dim3(plan->tb_threads);
+        cfg.dynamicSmemBytes = plan->tb_smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, plan->tb_kernel, targs);
+        if (e != cudaSuccess) return cuda_fail(e, "temporally blocked kernel launch");
+        const int64_t passes = (n_steps + plan->tb_k - 1) / plan->tb_k;
+        if (any_alias && ((passes - 1) & 1) == 0) {
+            // in place with an odd number of passes: the result is in the scratch copy
+            e = cudaMemcpyAsync(pout[0], t.zscr, inst_bytes(0), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
+        }
+        return CG_OK;
+    }
     const int wpb = plan->threads / 32;
     const int qgrid = (plan->sched == cgk::SCHED_STATIC) ? plan->nblocks : (plan->n_tiles + wpb - 1) / wpb;
     st = launch_stages(plan, plan->kernel, args, a, 0, G, qgrid, s);

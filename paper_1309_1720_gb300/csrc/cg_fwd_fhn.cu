@@ -1,11 +1,17 @@
-// Forward stage kernels of the FHN model (instantiations of cg_stepper.cuh).
-#include "cg_stepper.cuh"
+// Forward stage kernels of the FHN model (instantiations of cg_stepper.cuh and
+// cg_tblock.cuh).
+#include "cg_tblock.cuh"
 
 namespace cgk {
 
 const void *fwd_kernel_fhn(int stencil, int scheme, int cx)
 {
     return pick_fwd_kernel<MODEL_FHN>(stencil, scheme, cx);
+}
+
+const void *tb_kernel_fhn(int stencil, int scheme)
+{
+    return pick_tb_kernel<MODEL_FHN>(stencil, scheme);
 }
 
 }  // namespace cgk

@@ -39,7 +39,9 @@ struct Seg {
     int32_t mrow_b, mb0, mb1;
 };
 
-enum { SCHED_STATIC = 0, SCHED_QUEUE = 1 };
+// SCHED_TBLOCK: temporally blocked tiles (cg_tblock.cuh) for cg_run; the
+// plan's other kernels keep the static schedule.
+enum { SCHED_STATIC = 0, SCHED_QUEUE = 1, SCHED_TBLOCK = 2 };
 
 // Kernel argument block (passed by value).
 struct RunArgs {
@@ -95,6 +97,10 @@ const void *fwd_kernel_fhn(int stencil, int scheme, int cx);
 const void *fwd_kernel_bocf(int stencil, int scheme, int cx);
 const void *fwd_kernel_diff(int stencil, int scheme, int cx);
 const void *fwd_kernel_bocfh(int stencil, int scheme, int cx);
+const void *tb_kernel_fhn(int stencil, int scheme);
+const void *tb_kernel_bocf(int stencil, int scheme);
+const void *tb_kernel_diff(int stencil, int scheme);
+const void *tb_kernel_bocfh(int stencil, int scheme);
 const void *tlm_kernel_bocfh(int stencil, int scheme, int cx);
 const void *adj_kernel_bocfh(int stencil, int scheme, int cx);
 const void *tlm_kernel_fhn(int stencil, int scheme, int cx);

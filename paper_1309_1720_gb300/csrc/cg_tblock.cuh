@@ -1,0 +1,253 @@
+// Temporally blocked stepping for small grids (one instance, mirror or clamp
+// ghosts).
+//
+// On a small grid every stage of the persistent stage kernel costs about one
+// grid barrier plus one L2 round trip, far more than its arithmetic.  Here
+// each block owns a rectangular tile, loads it with a halo of H = K n_s cells
+// (K steps of n_s stages), advances the tile through all H stages in shared
+// memory, the region it updates shrinking by one cell per stage (a stage
+// reads one ring of neighbours), and writes the tile back: one grid barrier
+// per K steps instead of one per stage, at the price of recomputing the halo.
+// Ghost points (Fig. 1) at the domain's edges are refilled from the cells
+// they mirror after every stage, so the shrinking region never needs values
+// from another tile between barriers.
+//
+// Each cell's arithmetic is the stage kernel's: the model's local terms with
+// the centre weight folded in, the off-centre sums in the same order (5-point:
+// wy (S + N) then wx (W + E); 9-point: row sums R = W + E and
+// T = R + (wy/wd) C, then wd (T_south + T_north) and wx R), and the same
+// Runge-Kutta combine, so results equal cg_run's other launch shapes bit for
+// bit (the row sums are formed per cell here instead of once per row).
+#pragma once
+
+#include "cg_stepper.cuh"
+
+namespace cgk {
+
+struct TbArgs {
+    int32_t tx, ty;          // tile size (cells)
+    int32_t tiles_x;         // tiles along x (block b owns tile (b % tiles_x, b / tiles_x))
+    int32_t k;               // steps per pass
+    int32_t wmax;            // shared window capacity in cells (per array)
+    int32_t alias;           // z_in == z_out
+    int64_t n_steps;
+    double *zscr;            // scratch state for the ping-pong between passes
+};
+
+// Output buffer of pass p of P (see cg_run): the last pass writes z_out,
+// except in place where the first pass must not overwrite its input.
+__device__ __forceinline__ double *tb_dst(const RunArgs &a, const TbArgs &t, int64_t p, int64_t P)
+{
+    if (t.alias) return (p & 1) ? a.z_out : t.zscr;
+    return (((P - 1 - p) & 1) == 0) ? a.z_out : t.zscr;
+}
+
+// Window [w0, w1) along one axis for the tile [t0, t1) of an axis of n
+// cells and a halo of h: the halo, except that on a side where it reaches
+// the domain's edge the window stops at the ghost point (-1 or n) so that
+// the ghosts always have a slot.  Used on the host too.
+__host__ __device__ inline void tb_window(int t0, int t1, int n, int h, int &w0, int &w1)
+{
+    w0 = (t0 - h <= 0) ? -1 : t0 - h;
+    w1 = (t1 + h >= n) ? n + 1 : t1 + h;
+}
+
+template <int M, int ST, int NS>
+__global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs t)
+{
+    using MD = Model<M>;
+    constexpr int NV = MD::NV, ND = MD::ND;
+    extern __shared__ double sm[];
+    __shared__ Inst s_inst;
+    if (threadIdx.x == 0) s_inst = a.inst[0];
+    __syncthreads();
+    const Inst &I = s_inst;
+    const int nx = I.nx, ny = I.ny, bc = a.bc;
+    const bool mirror = (bc == CG_BC_MIRROR);
+    const int x0 = (blockIdx.x % t.tiles_x) * t.tx, y0 = (blockIdx.x / t.tiles_x) * t.ty;
+    const int x1 = min(x0 + t.tx, nx), y1 = min(y0 + t.ty, ny);    // tile [x0, x1) x [y0, y1)
+    const int Hmax = t.k * NS;
+    // window: the tile with Hmax cells of halo; where that reaches the
+    // domain's edge it ends at the ghost layer instead (tb_window)
+    int gx0, gx1, gy0, gy1;
+    tb_window(x0, x1, nx, Hmax, gx0, gx1);
+    tb_window(y0, y1, ny, Hmax, gy0, gy1);
+    const int WX = gx1 - gx0;
+    const int WS = t.wmax;
+    // arrays (each NV planes of WS): NS == 1: YA, YB; else Z, ACC, YA, YB
+    double *Z = sm;
+    double *ACC = Z + (NS > 1 ? NV * WS : 0);
+    double *YA = ACC + (NS > 1 ? NV * WS : 0);
+    double *YB = YA + NV * WS;
+    if (NS == 1) Z = YA;
+    auto at = [&](int gx, int gy) { return (gy - gy0) * WX + (gx - gx0); };
+
+    double wx[ND > 0 ? ND : 1], wy[ND > 0 ? ND : 1], wd[ND > 0 ? ND : 1], wt[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int f = 0; f < ND; ++f) {
+        wx[f] = I.wx[f];
+        wy[f] = I.wy[f];
+        wd[f] = I.wd[f];
+        wt[f] = I.wt[f];
+    }
+    const typename MD::Coef coef = MD::coef(I);
+    const double *mp = a.mp;
+    const int64_t plane = (int64_t)nx * ny;
+
+    // Ghost points of buffer B on the region [xl, xh) x [yl, yh): x ghosts of
+    // its rows first, then whole y-ghost rows (corners follow both flips).
+    auto fill_ghosts = [&](double *B, int xl, int xh, int yl, int yh) {
+        const int gx_lo = mirror ? 1 : 0, gx_hi = mirror ? nx - 2 : nx - 1;
+        const int gy_lo = mirror ? 1 : 0, gy_hi = mirror ? ny - 2 : ny - 1;
+        const bool left = (xl == 0), right = (xh == nx), bot = (yl == 0), top = (yh == ny);
+        const int nrow = yh - yl;
+        for (int q = threadIdx.x; q < 2 * nrow; q += blockDim.x) {
+            const int y = yl + (q >> 1);
+            const bool lft = (q & 1) == 0;
+            if (lft ? !left : !right) continue;
+            const int dst = at(lft ? -1 : nx, y), src = at(lft ? gx_lo : gx_hi, y);
+#pragma unroll
+            for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
+        }
+        __syncthreads();
+        const int cl = left ? xl - 1 : xl, ch = right ? xh + 1 : xh;
+        const int ncol = ch - cl;
+        for (int q = threadIdx.x; q < 2 * ncol; q += blockDim.x) {
+            const int x = cl + (q >> 1);
+            const bool lo = (q & 1) == 0;
+            if (lo ? !bot : !top) continue;
+            const int dst = at(x, lo ? -1 : ny), src = at(x, lo ? gy_lo : gy_hi);
+#pragma unroll
+            for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
+        }
+        __syncthreads();
+    };
+
+    const int64_t P = (t.n_steps + t.k - 1) / t.k;
+    uint32_t bad = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        const int64_t rest = t.n_steps - p * t.k;
+        const int kp = (int)(rest < t.k ? rest : t.k);
+        const int H = kp * NS;
+        const double *src = (p == 0) ? a.z_in : tb_dst(a, t, p - 1, P);
+        double *dst = tb_dst(a, t, p, P);
+        // load the window's domain cells: the tile plus H cells of halo
+        {
+            const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
+            const int w = xh - xl, n = w * (yh - yl);
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int gx = xl + c % w, gy = yl + c / w;
+#pragma unroll
+                for (int f = 0; f < NV; ++f) Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
+            }
+            __syncthreads();
+            fill_ghosts(Z, xl, xh, yl, yh);
+        }
+        double *Yin = Z;
+        for (int g = 1; g <= H; ++g) {
+            const int s = (g - 1) % NS;
+            const bool last = (s == NS - 1);
+            const int rad = H - g;
+            const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
+            const int w = xh - xl, n = w * (yh - yl);
+            double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
+            const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
+            // every thread runs the same number of iterations, so the model's
+            // warp-uniform paths see whole warps; surplus threads repeat the
+            // last cell and store nothing
+            for (int base = 0; base < n; base += blockDim.x) {
+                const int c = base + (int)threadIdx.x;
+                const bool act = c < n;
+                const int cc = act ? c : n - 1;
+                const int gx = xl + cc % w, gy = yl + cc / w;
+                const int li = at(gx, gy);
+                double zc[NV];
+#pragma unroll
+                for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
+                double F[NV];
+                MD::local(coef, mp, zc, F);
+#pragma unroll
+                for (int f = 0; f < ND; ++f) {
+                    const double *Q = Yin + f * WS;
+                    const double Wv = Q[li - 1], Ev = Q[li + 1];
+                    if (ST == CG_STENCIL9) {
+                        const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
+                        const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
+                        const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
+                        const double acc_f = fma(wd[f], Tl + Th, F[f]);
+                        F[f] = fma(wx[f], Wv + Ev, acc_f);
+                    } else {
+                        double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
+                        F[f] = fma(wx[f], Wv + Ev, acc_f);
+                    }
+                }
+                if (act) {
+#pragma unroll
+                    for (int f = 0; f < NV; ++f) {
+                        const int o = f * WS + li;
+                        if (NS == 1) {
+                            Yout[o] = fma(ca, F[f], zc[f]);
+                        } else if (s == 0) {
+                            ACC[o] = fma(ca, F[f], zc[f]);
+                            Yout[o] = fma(cyv, F[f], zc[f]);
+                        } else if (!last) {
+                            ACC[o] = fma(ca, F[f], ACC[o]);
+                            Yout[o] = fma(cyv, F[f], Z[o]);
+                        } else {
+                            Yout[o] = fma(ca, F[f], ACC[o]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            fill_ghosts(Yout, xl, xh, yl, yh);
+            Yin = Yout;
+        }
+        // write the tile back
+        {
+            const int w = x1 - x0, n = w * (y1 - y0);
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int gx = x0 + c % w, gy = y0 + c / w;
+#pragma unroll
+                for (int f = 0; f < NV; ++f) {
+                    const double v = Yin[f * WS + at(gx, gy)];
+                    bad |= nonfinite_bit(v);
+                    __stcg(dst + f * plane + (int64_t)gy * nx + gx, v);
+                }
+            }
+        }
+        if (p + 1 < P) {
+            const unsigned long long target = (unsigned long long)(p + 1) * a.nblocks_expect +
+                                              ((p == 0 && a.stuck_barrier) ? 1u : 0u);
+            if (!grid_barrier(reinterpret_cast<unsigned long long *>(a.sync), a.status, a.timeout_ns, target))
+                return;
+        }
+    }
+    bad = __any_sync(CG_FULL, bad != 0);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+}
+
+// Kernel table for one model: [stencil][scheme] (explicit schemes only).
+template <int M>
+inline const void *pick_tb_kernel(int stencil, int scheme)
+{
+#define CG_TB(ST)                                                                               \
+    switch (scheme) {                                                                           \
+    case CG_EULER: return reinterpret_cast<const void *>(&k_tblock<M, ST, 1>);                  \
+    case CG_HEUN: return reinterpret_cast<const void *>(&k_tblock<M, ST, 2>);                   \
+    case CG_RK4: return reinterpret_cast<const void *>(&k_tblock<M, ST, 4>);                    \
+    default: return nullptr;                                                                    \
+    }
+    if (stencil == CG_STENCIL5) { CG_TB(CG_STENCIL5) }
+    if (stencil == CG_STENCIL9) { CG_TB(CG_STENCIL9) }
+#undef CG_TB
+    return nullptr;
+}
+
+// Shared memory of k_tblock (bytes) for a window of wmax cells per array.
+inline size_t tb_smem_bytes(int nv, int ns, int wmax)
+{
+    return sizeof(double) * (size_t)nv * (ns == 1 ? 2 : 4) * (size_t)wmax;
+}
+
+}  // namespace cgk

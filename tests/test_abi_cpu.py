@@ -87,3 +87,20 @@ def test_gate_integrators_need_positive_time_constants(L):
     prm[8] = -1.0                           # tau_v+ < 0
     st, msg = _create(Problem(model=BOCF, dx=0.03, dt=0.05, scheme=RUSH_LARSEN, params=prm))
     assert st == 1 and "positive" in msg
+
+
+def test_temporal_blocking_rejected_before_device_work(L):
+    """Temporal blocking needs one instance, mirror or clamp ghosts and an
+    explicit scheme; the checks come before any device call."""
+    from paper_1309_1720_gb300 import Problem, FHN, BOCF, PERIODIC, RUSH_LARSEN, _lib
+    from paper_1309_1720_gb300._lib import CTuning
+    for prob in (Problem(model=FHN, bc=PERIODIC), Problem(model=BOCF, dx=0.03, dt=0.05, scheme=RUSH_LARSEN)):
+        c = prob.to_c()
+        tun = CTuning(0, 2, 256, 0, 2)
+        h = ctypes.c_void_p()
+        st = _lib.lib().cg_plan_create_tuned(ctypes.byref(c), ctypes.byref(tun), ctypes.byref(h))
+        assert st == 7, _lib.lib().cg_last_error().decode()
+    c = Problem(model=FHN).to_c()
+    h = ctypes.c_void_p()
+    st = _lib.lib().cg_plan_create_tuned(ctypes.byref(c), ctypes.byref(CTuning(0, 65, 256, 0, 2)), ctypes.byref(h))
+    assert st == 1

@@ -1,0 +1,134 @@
+"""Temporally blocked stepping (tuning schedule 2): each block advances its
+tile with a halo through k steps in shared memory between grid barriers.
+Its results must equal the stage kernel's bit for bit (same per-cell
+arithmetic) and the oracle's to 1e-12, for every model, stencil, explicit
+scheme and ghost rule, on ragged shapes, with step counts that leave a
+partial last pass, in place, and with the device-side checks."""
+import numpy as np
+import pytest
+
+from helpers import field_rel_err, oracle_run
+from paper_1309_1720_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _problem(model, nx, ny, stencil, scheme, bc):
+    from paper_1309_1720_gb300 import Problem, FHN, BOCF
+    if model == FHN:
+        return Problem(model=FHN, nx=nx, ny=ny, dx=0.04, stencil=stencil, scheme=scheme, bc=bc, dt=1e-4)
+    if model == BOCF:
+        return Problem(model=BOCF, nx=nx, ny=ny, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,), stencil=stencil,
+                       scheme=scheme, bc=bc, dt=0.05)
+    return Problem(model=3, nx=nx, ny=ny, dx=0.1, D=(1.0,), Dyy=(0.6,), stencil=stencil, scheme=scheme, bc=bc,
+                   dt=1e-3)
+
+
+def _state(model, nx, ny):
+    if model == 0:
+        return I.fhn_broken_wave(nx, ny, width=max(1, nx // 8))
+    if model == 1:
+        return I.bocf_spiral_cores(nx, ny, n_cores=2)
+    return (1.0 + 0.3 * I.uniform_pm1(9, nx * ny)).reshape(1, ny, nx)
+
+
+def _run(p, z0, n, tuning=None, inplace=False):
+    import torch
+    from paper_1309_1720_gb300 import Plan
+    plan = Plan(p, tuning=tuning)
+    z = torch.from_numpy(np.ascontiguousarray(z0)).cuda()
+    out = plan.run(z, n, out=z if inplace else None)
+    plan.status()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("model", [0, 1, 3])
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("shape", [(128, 128), (67, 45), (3, 7), (2, 2), (512, 2)])
+def test_tblock_bitwise_and_oracle(cuda_ok, model, stencil, scheme, bc, shape):
+    nx, ny = shape
+    p = _problem(model, nx, ny, stencil, scheme, bc)
+    z0 = _state(model, nx, ny)
+    n = 7
+    ref = _run(p, z0, n)
+    for k in (1, 2, 3):
+        g = _run(p, z0, n, tuning=dict(schedule=2, rows=k, threads=256))
+        assert np.array_equal(g, ref), k
+    assert field_rel_err(ref, oracle_run(p, z0, n)) <= TOL
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("n", [0, 1, 2, 5, 8])
+def test_tblock_in_place_and_step_counts(cuda_ok, k, n):
+    from paper_1309_1720_gb300 import FHN, RK4, STENCIL9
+    p = _problem(FHN, 70, 33, STENCIL9, RK4, 0)
+    z0 = _state(FHN, 70, 33)
+    ref = _run(p, z0, n)
+    assert np.array_equal(_run(p, z0, n, tuning=dict(schedule=2, rows=k), inplace=True), ref)
+    assert np.array_equal(_run(p, z0, n, tuning=dict(schedule=2, rows=k, threads=128)), ref)
+
+
+def test_tblock_c1_full_run(cuda_ok):
+    """The 128^2 explicit-Euler workload, 1000 steps, 4 steps per pass."""
+    from paper_1309_1720_gb300 import FHN
+    p = _problem(FHN, 128, 128, 0, 0, 0)
+    p.dt = 2e-4
+    z0 = I.fhn_broken_wave(128, 128, seed=0)
+    g = _run(p, z0, 1000, tuning=dict(schedule=2, rows=4))
+    assert np.array_equal(g, _run(p, z0, 1000))
+    assert field_rel_err(g, oracle_run(p, z0, 1000)) <= TOL
+
+
+def test_tblock_rejections(cuda_ok):
+    from paper_1309_1720_gb300 import CGError, Plan, FHN, BOCF, PERIODIC, RUSH_LARSEN
+    with pytest.raises(CGError):
+        Plan(_problem(FHN, 64, 64, 0, 2, PERIODIC), tuning=dict(schedule=2, rows=2))
+    with pytest.raises(CGError):
+        Plan(_problem(BOCF, 64, 64, 0, RUSH_LARSEN, 0), tuning=dict(schedule=2, rows=2))
+    with pytest.raises(CGError):
+        Plan([_problem(FHN, 64, 64, 0, 2, 0)] * 2, tuning=dict(schedule=2, rows=2))
+    with pytest.raises(CGError):                      # tile and halo exceed shared memory
+        Plan(_problem(BOCF, 2048, 2048, 1, 2, 0), tuning=dict(schedule=2, rows=8))
+
+
+def test_tblock_plan_keeps_tangents_and_adjoint(cuda_ok):
+    """A plan tuned for temporal blocking still runs the tangent-linear and
+    adjoint kernels (with the default launch shape)."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, FHN
+    p = _problem(FHN, 96, 80, 1, 2, 0)
+    z0 = torch.from_numpy(_state(FHN, 96, 80)).cuda()
+    dz = torch.from_numpy(I.unit_direction(z0.shape, 3)[None].copy()).cuda()
+    a, b = Plan(p), Plan(p, tuning=dict(schedule=2, rows=2))
+    for x, y in zip(a.tlm(z0, dz, 6), b.tlm(z0, dz, 6)):
+        assert torch.equal(x, y)
+    for x, y in zip(a.adjoint(z0, z0.clone(), 6), b.adjoint(z0, z0.clone(), 6)):
+        assert torch.equal(x, y)
+
+
+def test_tblock_device_checks(cuda_ok):
+    import torch
+    from paper_1309_1720_gb300 import CGError, Plan, FHN, FLAG_TEST_STUCK_BARRIER
+    p = _problem(FHN, 64, 64, 0, 2, 0)
+    z0 = _state(FHN, 64, 64)
+    z0[0, 10, 10] = np.nan
+    plan = Plan(p, tuning=dict(schedule=2, rows=2))
+    plan.run(torch.from_numpy(z0).cuda(), 5)
+    with pytest.raises(CGError) as ei:
+        plan.status()
+    assert ei.value.status == 5                      # CG_ENAN
+    q = _problem(FHN, 64, 64, 0, 2, 0)
+    q.flags = FLAG_TEST_STUCK_BARRIER
+    q.barrier_timeout_s = 0.2
+    stuck = Plan(q, tuning=dict(schedule=2, rows=2))
+    good = torch.from_numpy(_state(FHN, 64, 64)).cuda()
+    stuck.run(good, 6)
+    with pytest.raises(CGError) as ei:
+        stuck.status()
+    assert ei.value.status == 6                      # CG_ETIMEOUT
+    # the context is still usable
+    assert np.array_equal(_run(p, _state(FHN, 64, 64), 6, tuning=dict(schedule=2, rows=2)),
+                          _run(p, _state(FHN, 64, 64), 6))
