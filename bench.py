@@ -53,11 +53,13 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None, choices=["fhn", "bocf", "tlm", "adj"],
+    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None,
+                    choices=["fhn", "bocf", "tlm", "adj", "c1"],
                     help="run a short case twice and exit (for ncu captures): 20 steps of the "
                          "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), or on "
                          "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
-                         "16 steps (adj)")
+                         "16 steps (adj), or 200 steps of the 128^2 Euler problem with 4 steps per grid "
+                         "barrier (c1)")
     ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence", "orbit"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
@@ -475,16 +477,17 @@ def paper_experiments(which):
                 best = None
                 if N <= 1024:
                     for k in (2, 4, 8):
-                        try:
-                            tplan = Plan(prob, tuning=dict(schedule=2, rows=k))
-                        except Exception:
-                            continue
-                        tk = timed_step(tplan, z, 2000, reps=2) * 2000
-                        tplan.close()
-                        if best is None or tk < best[0]:
-                            best = (tk, k)
+                        for thr in (256, 512):
+                            try:
+                                tplan = Plan(prob, tuning=dict(schedule=2, rows=k, threads=thr))
+                            except Exception:
+                                continue
+                            tk = timed_step(tplan, z, 2000, reps=2) * 2000
+                            tplan.close()
+                            if best is None or tk < best[0]:
+                                best = (tk, k, thr)
                 if best is not None:
-                    tb[str(N)] = {"seconds": best[0], "k": best[1]}
+                    tb[str(N)] = {"seconds": best[0], "k": best[1], "threads": best[2]}
                 del z
             a = float(np.median(ts[:3]))
             b = float(np.median([t / N ** 2 for t, N in zip(ts, Ns) if N >= 2048]))
@@ -605,6 +608,16 @@ def main():
     out = torch.empty_like(z0)
     ws_t = plan.workspace()
 
+    if args.profile_case == "c1":
+        cp = api.Problem(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
+        plan = Plan(cp, tuning=dict(schedule=2, rows=4, threads=512))
+        z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
+        for _ in range(2):
+            plan.run(z, 200)
+        plan.status()
+        torch.cuda.synchronize()
+        print("profile case done")
+        return
     if args.profile_case in ("tlm", "adj"):
         n = 512
         gp = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, scheme=api.RK4, dt=2.5e-4)

@@ -50,10 +50,13 @@ DEFAULT_CANDIDATES: List[Dict] = [
     # temporal blocking (small grids): k steps per grid barrier in shared
     # memory; plan creation fails, and the candidate is skipped, where a
     # tile and its halo do not fit
-    dict(schedule=2, rows=1, threads=256),
     dict(schedule=2, rows=2, threads=256),
     dict(schedule=2, rows=4, threads=256),
     dict(schedule=2, rows=8, threads=256),
+    dict(schedule=2, rows=1, threads=512),
+    dict(schedule=2, rows=2, threads=512),
+    dict(schedule=2, rows=4, threads=512),
+    dict(schedule=2, rows=8, threads=512),
 ]
 
 

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
         const int gx_lo = mirror ? 1 : 0, gx_hi = mirror ? nx - 2 : nx - 1;
         const int gy_lo = mirror ? 1 : 0, gy_hi = mirror ? ny - 2 : ny - 1;
         const bool left = (xl == 0), right = (xh == nx), bot = (yl == 0), top = (yh == ny);
+        if (!(left || right || bot || top)) return;        // block-uniform: interior tiles skip both syncs
         const int nrow = yh - yl;
         for (int q = threadIdx.x; q < 2 * nrow; q += blockDim.x) {
             const int y = yl + (q >> 1);
