@@ -7,9 +7,12 @@
  *
  * on an nx x ny grid with no-flux boundaries (Eq. BC:N) imposed by ghost
  * points that flip stencil displacements back into the grid (Sect. 3,
- * Fig. 1), a 5-point or 9-point Laplacian (Eq. diffusion) and an explicit
- * fixed-step integrator (explicit Euler, Heun or classic RK4, Sect. 3), in
- * FP64 throughout, on one NVIDIA GB300 (sm_103a).  The problem statement
+ * Fig. 1) or with periodic ghosts, a 5-point or 9-point Laplacian (Eq.
+ * diffusion) and a fixed-step integrator (explicit Euler, Heun or classic
+ * RK4, or Rush-Larsen / implicit Euler on the four-field model's gates,
+ * Sect. 3), in FP64 throughout, on one NVIDIA GB300 (sm_103a).  Batches of
+ * uneven grids, exact tangent-linear and adjoint runs, a Newton-Krylov step
+ * and the right-hand side itself are exported too.  The problem statement
  * follows the paper's: model and its parameters, grid with dx and dy,
  * diffusivity D, time step dt, scheme, state in, state out, number of steps.
  *
