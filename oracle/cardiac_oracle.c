@@ -24,7 +24,7 @@
  * exact Jacobian of the discrete flow that the Newton-Krylov motivation of
  * Sect. 1 needs).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *  - stencil weights: alpha_a = 1 - 2 alpha_d (consistency), alpha_00 from
  *    the paper's balance condition; anisotropic tensors diag(Dxx, Dyy) use
  *    the form Dxx d_xx + Dyy d_yy + kappa h^2 d_xx d_yy,
