@@ -381,6 +381,22 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     plan.status()
     plan._ws = None
     torch.cuda.empty_cache()
+    # one Newton step on the period-T flow map: GMRES(30), one restart cycle,
+    # every Jacobian-vector product an exact tangent-linear run of T steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dz_a, hist = plan.newton_step(z, T, restart=30, max_restarts=1, rtol=1e-10)
+    torch.cuda.synchronize()
+    t_newton = time.perf_counter() - t0
+    # the same step with the stage Jacobians of the base trajectory stored
+    # once (2000 x 4 stages x 1 plane) and every JVP a tangent-only run
+    t0 = time.perf_counter()
+    dz_b, hist_b = plan.newton_step(z, T, restart=30, max_restarts=1, rtol=1e-10, linearized=True)
+    torch.cuda.synchronize()
+    t_newton_lin = time.perf_counter() - t0
+    newton_same = bool(torch.equal(dz_a, dz_b)) and hist == hist_b
+    del dz_a, dz_b
+    torch.cuda.empty_cache()
     g_plain = n * n * T / t_plain / 1e9
     rows["grad-512x512-5pt-rk4"] = {
         "gcups_plain": g_plain,
@@ -392,9 +408,16 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         "adjoint_seconds_T2000_all_stages_stored": t_adj_all,
         "adjoint_all_stages_workspace_gb": sz.value / 1e9,
         "adjoint_all_stages_vs_plain": (n * n * T / t_adj_all / 1e9) / g_plain,
+        "newton_gmres30_seconds": t_newton,
+        "newton_gmres30_iterations": len(hist) - 1,
+        "newton_gmres30_residual_reduction": hist[-1] / hist[0],
+        "newton_gmres30_linearized_seconds": t_newton_lin,
+        "newton_gmres30_linearized_bitwise_equal": newton_same,
         "note": "tlm: 64 tangents x 200 steps (rate); adjoint: full T = 2000 with ceil(sqrt(T)) checkpoints "
                 "(forward + segment recompute + reverse sweep), and with every stage input of the horizon "
-                "kept in HBM (forward with stores + reverse sweep)"}
+                "kept in HBM (forward with stores + reverse sweep); newton: one GMRES(30) cycle on the "
+                "T = 2000 flow map (wall time, 30 exact JVPs of 2000 steps each; linearized: stage "
+                "Jacobians stored by one primal run, JVPs advance the tangent alone)"}
     plan.close()
     return rows
 

@@ -269,6 +269,27 @@ cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t *bytes)
 cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, double *zT, double *dzT,
                      int32_t n_tangents, int64_t n_steps, void *workspace, void *stream);
 
+/* Linearized tangent-linear runs, for many Jacobian-vector products at one
+ * base point z0 (the Krylov iterations of a Newton step).  cg_tlm_linearize
+ * advances z0 -> zT (the same values as cg_run) and keeps the local Jacobian
+ * dN/dz of every RK stage in the workspace; cg_tlm_apply then advances
+ * n_tangents tangents dz0 -> dzT through the same n_steps with those
+ * Jacobians and no primal work, giving bit for bit the dzT of cg_tlm_run
+ * from the same z0.  The workspace (size from
+ * cg_tlm_linearized_workspace_size for the largest n_tangents to apply, and
+ * the same n_steps) holds n_steps * n_stages stored Jacobians of
+ * round32(NJ nx ny) doubles each (NJ = 1 FHN and diffusion, 10 BOCF) and
+ * must not be touched between the two calls; the plan, n_steps and the
+ * workspace pointer must be the same in both.  Layouts and in-place rules as
+ * cg_tlm_run.  CG_EINVAL for NULL buffers, negative counts, a misaligned
+ * workspace or partial overlap; CG_EUNSUPPORTED for batch plans and the gate
+ * integrators. */
+cg_status cg_tlm_linearized_workspace_size(cg_plan plan, int32_t n_tangents, int64_t n_steps, size_t *bytes);
+cg_status cg_tlm_linearize(cg_plan plan, const double *z0, double *zT, int64_t n_steps, void *workspace,
+                           void *stream);
+cg_status cg_tlm_apply(cg_plan plan, const double *dz0, double *dzT, int32_t n_tangents, int64_t n_steps,
+                       void *workspace, void *stream);
+
 /* ------------------------------------------------------ discrete adjoint */
 
 /* Bytes of workspace cg_adjoint_run needs (single-instance plans): the
@@ -312,6 +333,16 @@ cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t *bytes)
 cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
                                int32_t max_restarts, double rtol, double *dz, double *res_hist,
                                int32_t *n_iter, void *workspace, void *stream);
+
+/* The same Newton step with J_T v from cg_tlm_apply after one
+ * cg_tlm_linearize at z0: each Krylov iteration skips the primal run, at the
+ * cost of storing period_steps * n_stages stage Jacobians (workspace from
+ * cg_newton_linearized_workspace_size).  Results equal cg_newton_gmres_step's
+ * bit for bit. */
+cg_status cg_newton_linearized_workspace_size(cg_plan plan, int32_t restart, int64_t period_steps, size_t *bytes);
+cg_status cg_newton_gmres_step_linearized(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
+                                          int32_t max_restarts, double rtol, double *dz, double *res_hist,
+                                          int32_t *n_iter, void *workspace, void *stream);
 
 /* Deterministic vector kernels used by the Newton-Krylov step.
  * cg_dot: *result (device) = sum_i x[i] y[i], summed in a fixed order; the

@@ -59,6 +59,12 @@ _SIGS = {
     "cg_tlm_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    "cg_tlm_linearized_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_tlm_linearize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_tlm_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "cg_adjoint_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
     "cg_adjoint_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -69,6 +75,13 @@ _SIGS = {
                                             ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_newton_linearized_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                                           ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_newton_gmres_step_linearized": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                                                       ctypes.c_void_p]),
     "cg_dot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p]),
     "cg_axpby": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,

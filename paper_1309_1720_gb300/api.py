@@ -248,6 +248,11 @@ class Plan:
                                     n_t, int(n_steps), ws.data_ptr(), _stream_handle(stream)))
         return zT, dzT
 
+    def linearize(self, z0: torch.Tensor, n_steps: int, max_tangents: int = 1, stream=None) -> "Linearization":
+        """Advance z0 by n_steps keeping every stage's local Jacobian, for
+        repeated exact Jacobian-vector products at z0 (``Linearization``)."""
+        return Linearization(self, z0, n_steps, max_tangents, stream)
+
     def adjoint(self, z0: torch.Tensor, lamT: torch.Tensor, n_steps: int, checkpoint_every: int = 0,
                 stream=None):
         """Reverse-mode derivative of the n-step flow map: returns
@@ -268,25 +273,70 @@ class Plan:
         return lam0, dLdD
 
     def newton_step(self, z0: torch.Tensor, period_steps: int, restart: int = 30, max_restarts: int = 1,
-                    rtol: float = 1e-10, stream=None):
+                    rtol: float = 1e-10, linearized: bool = False, stream=None):
         """One Newton step on the period-T flow map by GMRES(restart) with
-        exact Jacobian-vector products.  Returns (dz, residual_history)."""
+        exact Jacobian-vector products (``linearized``: from stored stage
+        Jacobians, no primal work per Krylov iteration; same result).
+        Returns (dz, residual_history)."""
         assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        L = _lib.lib()
         sz = ctypes.c_size_t()
-        check(_lib.lib().cg_newton_workspace_size(self._h, int(restart), ctypes.byref(sz)))
+        if linearized:
+            check(L.cg_newton_linearized_workspace_size(self._h, int(restart), int(period_steps), ctypes.byref(sz)))
+        else:
+            check(L.cg_newton_workspace_size(self._h, int(restart), ctypes.byref(sz)))
         ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
         dz = torch.empty_like(z0)
         hist = (ctypes.c_double * (restart * max_restarts + 1))()
         nit = ctypes.c_int32()
-        check(_lib.lib().cg_newton_gmres_step(self._h, z0.data_ptr(), int(period_steps), int(restart),
-                                              int(max_restarts), float(rtol), dz.data_ptr(), hist,
-                                              ctypes.byref(nit), ws.data_ptr(), _stream_handle(stream)))
+        step = L.cg_newton_gmres_step_linearized if linearized else L.cg_newton_gmres_step
+        check(step(self._h, z0.data_ptr(), int(period_steps), int(restart), int(max_restarts), float(rtol),
+                   dz.data_ptr(), hist, ctypes.byref(nit), ws.data_ptr(), _stream_handle(stream)))
         return dz, [hist[i] for i in range(nit.value + 1)]
 
     def status(self, stream=None, workspace: Optional[torch.Tensor] = None, raise_on_error: bool = True) -> int:
+        """Device status flags of the last run on ``workspace`` (default: the
+        plan's own; 0 if nothing has run on it yet).  Raises CGError on a
+        timeout or a non-finite value unless ``raise_on_error`` is False."""
+        if workspace is None and self._ws is None:
+            return 0
         ws = self.workspace() if workspace is None else workspace
         flags = ctypes.c_uint32()
         st = _lib.lib().cg_read_status(self._h, ws.data_ptr(), _stream_handle(stream), ctypes.byref(flags))
         if raise_on_error:
             check(st)
         return int(flags.value)
+
+
+class Linearization:
+    """The stage Jacobians of one base trajectory z0 -> zT of a plan
+    (cg_tlm_linearize), kept in a workspace of their own; ``apply`` gives
+    dPhi/dz(z0) dz0 for up to ``max_tangents`` tangents at a time with no
+    primal work (cg_tlm_apply), bit for bit the tangents of ``Plan.tlm``."""
+
+    def __init__(self, plan: Plan, z0: torch.Tensor, n_steps: int, max_tangents: int = 1, stream=None):
+        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        self.plan = plan
+        self.n_steps = int(n_steps)
+        self.max_tangents = int(max_tangents)
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_tlm_linearized_workspace_size(plan._h, self.max_tangents, self.n_steps,
+                                                          ctypes.byref(sz)))
+        self.ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        self.zT = torch.empty_like(z0)
+        check(_lib.lib().cg_tlm_linearize(plan._h, z0.data_ptr(), self.zT.data_ptr(), self.n_steps,
+                                          self.ws.data_ptr(), _stream_handle(stream)))
+
+    def apply(self, dz0: torch.Tensor, dzT: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """dzT[i] = dPhi/dz(z0) dz0[i]; dz0 is [T, n_v, ny, nx] (or one state)."""
+        assert dz0.is_cuda and dz0.dtype == torch.float64 and dz0.is_contiguous()
+        n_t = dz0.numel() // self.zT.numel()
+        assert n_t * self.zT.numel() == dz0.numel() and n_t <= self.max_tangents
+        dzT = torch.empty_like(dz0) if dzT is None else dzT
+        check(_lib.lib().cg_tlm_apply(self.plan._h, dz0.data_ptr(), dzT.data_ptr(), n_t, self.n_steps,
+                                      self.ws.data_ptr(), _stream_handle(stream)))
+        return dzT
+
+    def status(self, stream=None) -> int:
+        """Device status of the linearizing and applying runs (raises on error)."""
+        return self.plan.status(stream=stream, workspace=self.ws)

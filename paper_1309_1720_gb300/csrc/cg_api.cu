@@ -1142,21 +1142,23 @@ const void *lookup_tlm_kernel(int kmodel, int stencil, int scheme, int cx)
     }
 }
 
-// Workspace of cg_tlm_run: header | primal scratch | J planes | tangent scratch.
 struct TlmLayout {
     size_t jbuf_off, tan_off, total;
-    int64_t tstride, tblk;
+    int64_t tstride, tblk, jstride;
 };
 
-TlmLayout tlm_layout(cg_plan P, int32_t n_tan)
+// Workspace of the tangent-linear runs: header | primal scratch | stage
+// Jacobians (one stage, or n_jstages when linearized) | tangent scratch.
+TlmLayout tlm_layout(cg_plan P, int32_t n_tan, int64_t n_jstages = 1)
 {
     const Inst &I = P->inst[0];
     const int64_t plane = (int64_t)I.nx * I.ny;
     TlmLayout L;
     L.tstride = (int64_t)P->nv * plane;
     L.tblk = round32((int64_t)cgk::SCRATCH_PLANES * P->nv * plane);
+    L.jstride = round32(std::max(1, cgk::model_nj(P->model)) * plane);
     L.jbuf_off = cgk::WS_HEADER + (size_t)P->scratch_elems * sizeof(double);
-    L.tan_off = L.jbuf_off + (size_t)round32(std::max(1, cgk::model_nj(P->model)) * plane) * sizeof(double);
+    L.tan_off = L.jbuf_off + (size_t)std::max<int64_t>(1, n_jstages) * (size_t)L.jstride * sizeof(double);
     L.total = L.tan_off + (size_t)n_tan * (size_t)L.tblk * sizeof(double);
     return L;
 }
@@ -1253,6 +1255,82 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
     t.tblk = L.tblk;
     void *args[] = {&a, &t};
     return launch_stages(plan, k, args, a, 0, n_steps * plan->ns, plan->nblocks, s);
+}
+
+CG_API cg_status cg_tlm_linearized_workspace_size(cg_plan plan, int32_t n_tangents, int64_t n_steps, size_t *bytes)
+{
+    if (!plan || !bytes || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    if (gate_scheme(plan->scheme))
+        return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
+    *bytes = tlm_layout(plan, n_tangents, n_steps * plan->ns).total;
+    return CG_OK;
+}
+
+// Shared body of cg_tlm_linearize (primal, every stage's Jacobian kept) and
+// cg_tlm_apply (tangents only, with those Jacobians).
+static cg_status tlm_linearized(cg_plan plan, const double *z0, double *zT, const double *dz0, double *dzT,
+                                int32_t n_tangents, int64_t n_steps, bool apply, void *workspace, void *stream)
+{
+    if (!plan) return fail(CG_EINVAL, "plan is NULL");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
+    if (gate_scheme(plan->scheme))
+        return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
+    if (!workspace || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (apply ? (n_tangents > 0 && (!dz0 || !dzT)) : (!z0 || !zT)) return fail(CG_EINVAL, "NULL buffer");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(CG_EINVAL, "workspace must be 256-byte aligned");
+    const TlmLayout L = tlm_layout(plan, n_tangents, n_steps * plan->ns);
+    const size_t sbytes = (size_t)L.tstride * sizeof(double);
+    const size_t tbytes = sbytes * (size_t)n_tangents;
+    if (!apply && overlaps(z0, zT, sbytes)) return fail(CG_EINVAL, "input and output partially overlap");
+    if (apply && n_tangents && overlaps(dz0, dzT, tbytes)) return fail(CG_EINVAL, "input and output partially overlap");
+    if (plan->ns == 1 && n_steps > 0 && (apply ? (n_tangents && dz0 == dzT) : (z0 == zT)))
+        return fail(CG_EINVAL, "in-place tangent-linear runs need a multi-stage scheme");
+    cg_status st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    if (n_steps == 0) {
+        if (!apply && z0 != zT) e = cudaMemcpyAsync(zT, z0, sbytes, cudaMemcpyDeviceToDevice, s);
+        if (apply && n_tangents && dz0 != dzT) e = cudaMemcpyAsync(dzT, dz0, tbytes, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    if (apply && n_tangents == 0) return CG_OK;
+    const void *k = lookup_tlm_kernel(plan->kmodel, plan->stencil, plan->scheme, plan->cx);
+    if (!k) return fail(CG_EUNSUPPORTED, "no tangent-linear kernel for this problem");
+    st = check_coresident(plan, k);
+    if (st != CG_OK) return st;
+    RunArgs a;
+    base_args(plan, a, apply ? nullptr : z0, apply ? nullptr : zT, ws);
+    a.parity = (int32_t)((n_steps - 1) & 1);
+    cgk::TlmArgs t;
+    std::memset(&t, 0, sizeof t);
+    t.dz_in = apply ? dz0 : nullptr;
+    t.dz_out = apply ? dzT : nullptr;
+    t.jbuf = reinterpret_cast<double *>(ws + L.jbuf_off);
+    t.tws = reinterpret_cast<double *>(ws + L.tan_off);
+    t.n_tan = apply ? n_tangents : 0;
+    t.skip_primal = apply ? 1 : 0;
+    t.tstride = L.tstride;
+    t.tblk = L.tblk;
+    t.jstride = L.jstride;
+    void *args[] = {&a, &t};
+    return launch_stages(plan, k, args, a, 0, n_steps * plan->ns, plan->nblocks, s);
+}
+
+CG_API cg_status cg_tlm_linearize(cg_plan plan, const double *z0, double *zT, int64_t n_steps, void *workspace,
+                                  void *stream)
+{
+    return tlm_linearized(plan, z0, zT, nullptr, nullptr, 0, n_steps, false, workspace, stream);
+}
+
+CG_API cg_status cg_tlm_apply(cg_plan plan, const double *dz0, double *dzT, int32_t n_tangents, int64_t n_steps,
+                              void *workspace, void *stream)
+{
+    return tlm_linearized(plan, nullptr, nullptr, dz0, dzT, n_tangents, n_steps, true, workspace, stream);
 }
 
 // ------------------------------------------------------------------ adjoint

@@ -113,37 +113,58 @@ struct Dev {
 
 }  // namespace
 
-CG_API cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t *bytes)
+// Bytes of the tangent-linear workspace at the front of the Newton workspace:
+// one stage Jacobian reused (lin = false) or every stage's kept (lin = true).
+static cg_status newton_sizes(cg_plan plan, int32_t restart, bool lin, int64_t period_steps, size_t *tws,
+                              size_t *total)
 {
-    if (!plan || !bytes || restart < 1) return err(CG_EINVAL, "cg_newton_workspace_size: bad argument");
     int64_t off[2];
+    if (cg_plan_n_instances(plan) != 1) return err(CG_EUNSUPPORTED, "Newton steps need a single-instance plan");
     cg_status st = cg_batch_offsets(plan, off);
     if (st != CG_OK) return st;
-    if (cg_plan_n_instances(plan) != 1) return err(CG_EUNSUPPORTED, "Newton steps need a single-instance plan");
-    size_t tws = 0;
-    st = cg_tlm_workspace_size(plan, 1, &tws);
+    st = lin ? cg_tlm_linearized_workspace_size(plan, 1, period_steps, tws) : cg_tlm_workspace_size(plan, 1, tws);
     if (st != CG_OK) return st;
-    const size_t n = (size_t)off[1];
-    const size_t vec = (n + 31) / 32 * 32 * sizeof(double);
-    *bytes = (tws + 255) / 256 * 256 + vec * (size_t)(restart + 4) + 4096;
+    *tws = (*tws + 255) / 256 * 256;
+    const size_t vec = ((size_t)off[1] + 31) / 32 * 32 * sizeof(double);
+    *total = *tws + vec * (size_t)(restart + 4) + 4096;
     return CG_OK;
 }
 
-CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
-                                      int32_t max_restarts, double rtol, double *dz, double *res_hist,
-                                      int32_t *n_iter, void *workspace, void *stream)
+CG_API cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t *bytes)
+{
+    if (!plan || !bytes || restart < 1) return err(CG_EINVAL, "cg_newton_workspace_size: bad argument");
+    size_t tws = 0;
+    return newton_sizes(plan, restart, false, 0, &tws, bytes);
+}
+
+CG_API cg_status cg_newton_linearized_workspace_size(cg_plan plan, int32_t restart, int64_t period_steps,
+                                                     size_t *bytes)
+{
+    if (!plan || !bytes || restart < 1 || period_steps < 1)
+        return err(CG_EINVAL, "cg_newton_linearized_workspace_size: bad argument");
+    size_t tws = 0;
+    return newton_sizes(plan, restart, true, period_steps, &tws, bytes);
+}
+
+// One GMRES Newton step.  lin = false: every J v is a tangent-linear run that
+// recomputes the primal trajectory; lin = true: one linearizing run keeps
+// every stage's Jacobian, and each J v advances the tangent alone.  Both
+// apply the same arithmetic to every tangent, so their results agree bit for
+// bit.
+static cg_status gmres_step(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
+                            int32_t max_restarts, double rtol, double *dz, double *res_hist, int32_t *n_iter,
+                            void *workspace, void *stream, bool lin)
 {
     if (!plan || !z0 || !dz || !workspace || period_steps < 1 || restart < 1 || max_restarts < 1 || !(rtol > 0))
         return err(CG_EINVAL, "cg_newton_gmres_step: bad argument");
     int64_t off[2];
-    if (cg_plan_n_instances(plan) != 1) return err(CG_EUNSUPPORTED, "Newton steps need a single-instance plan");
     cg_status st = cg_batch_offsets(plan, off);
     if (st != CG_OK) return st;
     const int64_t n = off[1];
-    size_t tws = 0;
-    st = cg_tlm_workspace_size(plan, 1, &tws);
+    size_t tws = 0, total = 0;
+    st = newton_sizes(plan, restart, lin, period_steps, &tws, &total);
     if (st != CG_OK) return st;
-    tws = (tws + 255) / 256 * 256;
+    (void)total;
     const size_t vec = (size_t)(n + 31) / 32 * 32;
     char *base = reinterpret_cast<char *>(workspace);
     double *V = reinterpret_cast<double *>(base + tws);              // restart + 1 basis vectors
@@ -156,8 +177,15 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
     d.dres = d.dpart + DOT_BLOCKS;
     const int m = restart;
 
+    // J v: vout = J_T(z0) vin
+    auto jvp = [&](const double *vin, double *vout) {
+        return lin ? cg_tlm_apply(plan, vin, vout, 1, period_steps, base, stream)
+                   : cg_tlm_run(plan, z0, vin, zT, vout, 1, period_steps, base, stream);
+    };
+
     // b = -(Phi_T(z0) - z0), stored in w
-    st = cg_run(plan, z0, phi, period_steps, base, stream);
+    st = lin ? cg_tlm_linearize(plan, z0, phi, period_steps, base, stream)
+             : cg_run(plan, z0, phi, period_steps, base, stream);
     if (st != CG_OK) return st;
     cudaError_t e = cudaMemcpyAsync(w, z0, sizeof(double) * n, cudaMemcpyDeviceToDevice, d.s);
     if (e != cudaSuccess) return cuda_err(e);
@@ -190,7 +218,7 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
             double *vj = V + vec * j;
             double *vn = V + vec * (j + 1);
             // vn = J_T vj - vj
-            st = cg_tlm_run(plan, z0, vj, zT, vn, 1, period_steps, base, stream);
+            st = jvp(vj, vn);
             if (st != CG_OK) return st;
             if ((st = d.axpby(-1.0, vj, 1.0, vn, n)) != CG_OK) return st;
             for (int i = 0; i <= j; ++i) {
@@ -238,7 +266,7 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
             if ((st = d.axpby(y[i], V + vec * i, 1.0, dz, n)) != CG_OK) return st;
         if (rnorm <= rtol * bnorm) break;
         // true residual for the restart: r = b - A dz
-        st = cg_tlm_run(plan, z0, dz, zT, phi, 1, period_steps, base, stream);
+        st = jvp(dz, phi);
         if (st != CG_OK) return st;
         if ((st = d.axpby(1.0, dz, -1.0, phi, n)) != CG_OK) return st;      // phi = dz - J dz
         if ((st = d.axpby(1.0, w, 1.0, phi, n)) != CG_OK) return st;        // + b
@@ -248,4 +276,20 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
     }
     if (n_iter) *n_iter = iters;
     return cuda_err(cudaStreamSynchronize(d.s));
+}
+
+CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t period_steps, int32_t restart,
+                                      int32_t max_restarts, double rtol, double *dz, double *res_hist,
+                                      int32_t *n_iter, void *workspace, void *stream)
+{
+    return gmres_step(plan, z0, period_steps, restart, max_restarts, rtol, dz, res_hist, n_iter, workspace, stream,
+                      false);
+}
+
+CG_API cg_status cg_newton_gmres_step_linearized(cg_plan plan, const double *z0, int64_t period_steps,
+                                                 int32_t restart, int32_t max_restarts, double rtol, double *dz,
+                                                 double *res_hist, int32_t *n_iter, void *workspace, void *stream)
+{
+    return gmres_step(plan, z0, period_steps, restart, max_restarts, rtol, dz, res_hist, n_iter, workspace, stream,
+                      true);
 }

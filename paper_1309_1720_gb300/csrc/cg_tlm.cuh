@@ -7,6 +7,10 @@
 // (KIND_PRIMAL_J); it then advances every tangent on the same cells with
 // dF = D L dY + J dY (KIND_TANGENT), reading J back from its own stores, so
 // the primal and all tangents of a stage need one grid barrier, not two.
+//
+// Linearized mode: a first run keeps every stage's Jacobian (jstride > 0)
+// and later runs advance tangents only (skip_primal), reading them back, for
+// repeated Jacobian-vector products at one base point.
 #pragma once
 
 #include "cg_stepper.cuh"
@@ -17,11 +21,12 @@ struct TlmArgs {
     const double *dz_in;   // n_tan tangent states, each n_v planes
     double *dz_out;
     double *tws;           // n_tan scratch blocks of tblk doubles
-    double *jbuf;          // NJ planes of stage Jacobian entries
+    double *jbuf;          // NJ planes of stage Jacobian entries (per stage when jstride > 0)
     int32_t n_tan;
-    int32_t pad;
+    int32_t skip_primal;   // 1: tangents only, with the Jacobians a linearizing run stored
     int64_t tstride;       // doubles per tangent state
     int64_t tblk;          // doubles per tangent scratch block
+    int64_t jstride;       // 0: one stage buffer reused; else doubles between stages' Jacobians
 };
 
 template <int M, int ST, int NS, int CX>
@@ -45,28 +50,33 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
     uint32_t bad = 0;
     auto seg_k = [&](int k) { return (k - sbeg) < SEG_CACHE ? cache.seg[k - sbeg] : a.segs[k]; };
 
-    auto stage = [&](int s, int64_t step) {
-        const Bufs Bp{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off};
-        for (int k = sbeg; k < send; ++k) {
-            const Seg sg = seg_k(k);
-            bad |= SP::seg(a, I, mp, Bp, t.jbuf, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
-                           sg.mb0, sg.mb1, s, step, lane);
+    auto stage = [&](int64_t g) {
+        const int s = (int)(g % NS);
+        const int64_t step = g / NS;
+        double *jb = t.jbuf + g * t.jstride;
+        if (!t.skip_primal) {
+            const Bufs Bp{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off};
+            for (int k = sbeg; k < send; ++k) {
+                const Seg sg = seg_k(k);
+                bad |= SP::seg(a, I, mp, Bp, jb, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
+                               sg.mb0, sg.mb1, s, step, lane);
+            }
         }
         for (int q = 0; q < t.n_tan; ++q) {
             const Bufs Bt{t.dz_in + q * t.tstride, t.dz_out + q * t.tstride, t.tws + q * t.tblk};
             for (int k = sbeg; k < send; ++k) {
                 const Seg sg = seg_k(k);
-                bad |= STn::seg(a, I, mp, Bt, t.jbuf, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1,
+                bad |= STn::seg(a, I, mp, Bt, jb, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1,
                                 sg.mrow_b, sg.mb0, sg.mb1, s, step, lane);
             }
         }
     };
 
     if (!a.persistent) {
-        stage((int)(a.g_begin % NS), a.g_begin / NS);
+        stage(a.g_begin);
     } else {
         for (int64_t g = a.g_begin; g < a.g_end; ++g) {
-            stage((int)(g % NS), g / NS);
+            stage(g);
             if (g + 1 < a.g_end && !stage_sync(a, g, g == a.g_begin)) return;
         }
     }

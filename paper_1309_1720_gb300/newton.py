@@ -12,7 +12,8 @@ dt = T / n_steps, by Newton's method on the bordered system
 shift along the orbit; F(Phi_T z) is dPhi_T/dT of the continuous flow).
 Each Newton step solves it by restarted GMRES with modified Gram-Schmidt.
 Every vector operation runs in the library's kernels: J v by the
-tangent-linear run (exact, not a difference of nearby solutions), F by
+tangent-linear run (exact, not a difference of nearby solutions; by default
+from the stage Jacobians one linearizing run keeps per iterate), F by
 cg_rhs, inner products by cg_dot (fixed summation order) and updates by
 cg_axpby; only the (m+1) x m Hessenberg least-squares problem and the
 bordering scalars live on the host.
@@ -57,13 +58,17 @@ def _givens(a: float, b: float):
 
 def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: int, tol: float = 1e-11,
                    max_newton: int = 12, restart: int = 30, max_restarts: int = 4, gmres_rtol: float = 1e-7,
-                   verbose: bool = False):
+                   linearized: bool = True, verbose: bool = False):
     """Newton-Krylov search for a periodic orbit through (z0, T0).
 
     ``problem`` is a single-instance problem whose ``dt`` is ignored (each
-    iterate uses dt = T / n_steps).  Returns (z, T, history) with history a
-    list of dicts (Newton iteration, relative residual |Phi_T(z) - z| / |z|,
-    T, GMRES iterations, final GMRES relative residual).
+    iterate uses dt = T / n_steps).  ``linearized``: each Newton iterate
+    keeps the stage Jacobians of its trajectory (n_steps x stages x NJ
+    planes of device memory) so that every J v advances the tangent alone;
+    otherwise each J v re-runs the primal.  Both give the same iterates bit
+    for bit.  Returns (z, T, history) with history a list of dicts (Newton
+    iteration, relative residual |Phi_T(z) - z| / |z|, T, GMRES iterations,
+    final GMRES relative residual).
     """
     assert z0.is_cuda and z0.dtype == torch.float64
     vec = _Vec()
@@ -78,7 +83,8 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
     for it in range(max_newton + 1):
         plan = plan_for(T)
         zs = z.view(shape)
-        zT = plan.run(zs, n_steps).reshape(-1)
+        lin = plan.linearize(zs, n_steps) if linearized else None
+        zT = (lin.zT if linearized else plan.run(zs, n_steps)).reshape(-1)
         r = zT.clone()
         vec.axpby(-1.0, z, 1.0, r)                        # r = Phi_T(z) - z
         rn = math.sqrt(vec.dot(r, r))
@@ -88,6 +94,8 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
         if verbose:
             print("newton %d  |r|/|z| = %.3e  T = %.12g" % (it, rn / zn, T))
         if rn / zn <= tol or it == max_newton:
+            if lin is not None:
+                lin.status()
             plan.status()
             plan.close()
             break
@@ -96,7 +104,8 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
         plan.status()
 
         def apply(v: torch.Tensor, s: float):
-            _, jv = plan.tlm(zs, v.view((1,) + tuple(shape)), n_steps)
+            v1 = v.view((1,) + tuple(shape))
+            jv = lin.apply(v1) if linearized else plan.tlm(zs, v1, n_steps)[1]
             w = jv.reshape(-1)
             vec.axpby(-1.0, v, 1.0, w)                    # (J - I) v
             vec.axpby(s, b, 1.0, w)                       # + F(Phi_T z) s
@@ -164,6 +173,9 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
                 break
         rec["gmres_iterations"] = n_it
         rec["gmres_rel_residual"] = gres
+        if lin is not None:
+            lin.status()
+            lin = None
         plan.close()
         vec.axpby(1.0, dz, 1.0, z)
         T += dT

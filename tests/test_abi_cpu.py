@@ -104,3 +104,17 @@ def test_temporal_blocking_rejected_before_device_work(L):
     h = ctypes.c_void_p()
     st = _lib.lib().cg_plan_create_tuned(ctypes.byref(c), ctypes.byref(CTuning(0, 65, 256, 0, 2)), ctypes.byref(h))
     assert st == 1
+
+
+def test_linearized_tangent_entry_points_reject_null_plan(L):
+    """The linearized tangent-linear and Newton entry points check their
+    arguments before touching the device."""
+    sz = ctypes.c_size_t()
+    assert L.cg_tlm_linearized_workspace_size(None, 1, 10, ctypes.byref(sz)) == 1
+    assert L.cg_tlm_linearize(None, None, None, 10, None, None) == 1
+    assert L.cg_tlm_apply(None, None, None, 1, 10, None, None) == 1
+    assert L.cg_newton_linearized_workspace_size(None, 30, 10, ctypes.byref(sz)) == 1
+    hist = (ctypes.c_double * 2)()
+    nit = ctypes.c_int32()
+    assert L.cg_newton_gmres_step_linearized(None, None, 10, 30, 1, 1e-8, None, hist, ctypes.byref(nit),
+                                             None, None) == 1
