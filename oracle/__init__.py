@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FHN, BOCF, DIFFUSION = 0, 1, 3
+FHN, BOCF, KARMA, DIFFUSION = 0, 1, 2, 3
 ST5, ST9 = 0, 1
 MIRROR, CLAMP, PERIODIC = 0, 1, 2
 EULER, HEUN, RK4, RUSH_LARSEN, IMPLICIT_EULER = 0, 1, 2, 3, 4
@@ -103,9 +103,10 @@ def problem(model=FHN, nx=64, ny=64, dx=0.04, dy=None, Dxx=None, Dyy=None,
             stencil=ST5, alpha_d=1.0 / 6.0, bc=MIRROR, scheme=EULER, dt=1e-4,
             params=None, variant=AS_WRITTEN) -> Problem:
     """Build the oracle's problem record.  Defaults: FHN diffusivities
-    (D_u, D_v) = (1, 1.5); BOCF D_u = 1.171e-3 cm^2/ms, gates not diffusive.
-    ``variant=TANH_AS_HK`` selects the Bueno-Orovio model with its tanh terms
-    replaced by smoothed steps (Sect. 6)."""
+    (D_u, D_v) = (1, 1.5); BOCF D_u = 1.171e-3 cm^2/ms, gates not diffusive;
+    Karma gamma = D_u = 1.1e-3 cm^2/ms, v not diffusive.
+    ``variant=TANH_AS_HK`` selects the Bueno-Orovio or Karma model with its
+    tanh terms replaced by smoothed steps (Sect. 6)."""
     p = Problem()
     p.variant = variant
     p.model, p.stencil, p.bc, p.scheme = model, stencil, bc, scheme
@@ -115,7 +116,7 @@ def problem(model=FHN, nx=64, ny=64, dx=0.04, dy=None, Dxx=None, Dyy=None,
     p.alpha_d = alpha_d
     p.dt = dt
     if Dxx is None:
-        Dxx = {FHN: [1.0, 1.5], BOCF: [1.171e-3, 0, 0, 0], DIFFUSION: [1.0]}[model]
+        Dxx = {FHN: [1.0, 1.5], BOCF: [1.171e-3, 0, 0, 0], KARMA: [1.1e-3, 0], DIFFUSION: [1.0]}[model]
     if Dyy is None:
         Dyy = Dxx
     for i in range(MAXF):

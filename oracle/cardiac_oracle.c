@@ -15,6 +15,7 @@
  *   ghost points by flipping displacements back into the grid  Sect. 3, Fig. 1
  *   nine-point Laplacian with diagonal weight alpha_d           Eq. (diffusion)
  *   FitzHugh-Nagumo                                             Eq. (fhn)
+ *   two-variable Karma model                                    Eq. (karma), Sect. 2
  *   Bueno-Orovio-Cherry-Fenton with cubic smoothed steps H_k    Eq. (bochfe), Sect. 2
  *   explicit Euler, Heun, classic RK4, fixed dt                 Sect. 3
  *   Rush-Larsen and implicit Euler on the Bueno-Orovio gates    Sect. 3, Table 2
@@ -37,15 +38,19 @@
  *    v, w, s (linear in themselves) are advanced with u frozen at the start
  *    of the step;
  *  - the tanh variant replaces (1 + tanh(kk x))/2 by H_{kk/3}(x), the smooth
- *    step with the same value and slope at x = 0.
- * Model constants of the Bueno-Orovio epicardial set are not printed in the
- * paper: parity unpinned for those values.
+ *    step with the same value and slope at x = 0 (Karma: tanh(u - u_h) by
+ *    2 H_{1/3}(u - u_h) - 1);
+ *  - Karma: only u diffuses (gamma = D_u); v^M is pow(v, M) as written.
+ * Model constants of the Bueno-Orovio epicardial set, and the Karma model's
+ * tau_u, tau_v, u*, u_h, u_v, are not printed in the paper (it cites the
+ * models' own papers): parity unpinned for those values; the Karma pins fix
+ * the form of Eq. (karma) for any constants.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_FHN = 0, ORC_BOCF = 1, ORC_DIFFUSION = 3 };
+enum { ORC_FHN = 0, ORC_BOCF = 1, ORC_KARMA = 2, ORC_DIFFUSION = 3 };
 enum { ORC_ST5 = 0, ORC_ST9 = 1 };
 enum { ORC_MIRROR = 0, ORC_CLAMP = 1, ORC_PERIODIC = 2 };
 enum { ORC_EULER = 0, ORC_HEUN = 1, ORC_RK4 = 2, ORC_RUSH_LARSEN = 3, ORC_IMPLICIT_EULER = 4 };
@@ -60,7 +65,7 @@ typedef struct {
     double dx, dy, alpha_d, dt;
     double Dxx[ORC_MAXF], Dyy[ORC_MAXF];
     double params[ORC_MAXP];
-    int variant;        /* ORC_AS_WRITTEN or ORC_TANH_AS_HK (Bueno-Orovio only) */
+    int variant;        /* ORC_AS_WRITTEN or ORC_TANH_AS_HK (Bueno-Orovio, Karma) */
 } orc_problem;
 
 /* ------------------------------------------------------------------ models */
@@ -70,6 +75,7 @@ int orc_n_fields(int model)
     switch (model) {
     case ORC_FHN: return 2;
     case ORC_BOCF: return 4;
+    case ORC_KARMA: return 2;
     case ORC_DIFFUSION: return 1;
     default: return -1;
     }
@@ -85,11 +91,16 @@ enum {
     B_NPARAMS
 };
 
+/* Karma parameter order: the time constants, u*, u_h, u_v of Eq. (karma),
+ * then Re, M and the H_k sharpness k. */
+enum { K_TU, K_TV, K_USTAR, K_UH, K_UV, K_RE, K_M, K_K, K_NPARAMS };
+
 int orc_n_params(int model)
 {
     switch (model) {
     case ORC_FHN: return 3;           /* eps, a1, a0 */
     case ORC_BOCF: return B_NPARAMS;
+    case ORC_KARMA: return K_NPARAMS;
     case ORC_DIFFUSION: return 0;
     default: return -1;
     }
@@ -117,6 +128,15 @@ int orc_default_params(int model, double *out)
         p[B_K] = 28.4;   /* Sect. 2: k = 28.4 */
         memcpy(out, p, sizeof p);
         return B_NPARAMS;
+    }
+    if (model == ORC_KARMA) {
+        /* Sect. 2 prints (Re, M, gamma) = (1, 6, 0.0011 cm^2/ms) (gamma is
+         * D_u and lives in Dxx/Dyy) and k = 28.4; tau_u = 2.5 ms,
+         * tau_v = 250 ms, u* = 1.5415, u_h = 3, u_v = 1 are the cited
+         * model's values. */
+        out[K_TU] = 2.5; out[K_TV] = 250.0; out[K_USTAR] = 1.5415; out[K_UH] = 3.0; out[K_UV] = 1.0;
+        out[K_RE] = 1.0; out[K_M] = 6.0; out[K_K] = 28.4;
+        return K_NPARAMS;
     }
     if (model == ORC_DIFFUSION) return 0;
     return -1;
@@ -153,6 +173,20 @@ static double half_tanh(const orc_problem *p, double u, double kk, double cc, do
     double th = tanh(kk * (u - cc));
     *d = kk * (1.0 - th * th) / 2.0;
     return (1.0 + th) / 2.0;
+}
+
+/* tanh(u - u_h) of Eq. (karma), or 2 H_{1/3}(u - u_h) - 1 under the tanh
+ * variant of Sect. 6; *d (if not NULL) receives the derivative in u. */
+static double karma_tanh(const orc_problem *p, double u, double *d)
+{
+    double x = u - p->params[K_UH];
+    if (p->variant == ORC_TANH_AS_HK) {
+        if (d) *d = 2.0 * orc_dHk(x, 1.0 / 3.0);
+        return 2.0 * orc_Hk(x, 1.0 / 3.0) - 1.0;
+    }
+    double th = tanh(x);
+    if (d) *d = 1.0 - th * th;
+    return th;
 }
 
 /* Eq. (bochfe) with the currents and the alpha/beta gate form: f = N[z] at
@@ -208,6 +242,14 @@ void orc_pointwise(const orc_problem *p, const double *z, double *f)
         f[0] = 0.0;
         return;
     }
+    if (p->model == ORC_KARMA) {
+        /* Eq. (karma) */
+        double u = z[0], v = z[1], k = q[K_K];
+        double th = karma_tanh(p, u, NULL);
+        f[0] = (u * u / 2.0 * (1.0 - th) * (q[K_USTAR] - pow(v, q[K_M])) - u) / q[K_TU];
+        f[1] = ((1.0 / (1.0 - exp(-q[K_RE])) - v) * orc_Hk(u - q[K_UV], k) - v * orc_Hk(q[K_UV] - u, k)) / q[K_TV];
+        return;
+    }
     bocf_eval(p, z, f, NULL, NULL);
 }
 
@@ -224,6 +266,20 @@ void orc_pointwise_jac(const orc_problem *p, const double *z, double *J)
     }
     if (p->model == ORC_DIFFUSION) {
         J[0] = 0.0;
+        return;
+    }
+    if (p->model == ORC_KARMA) {
+        /* f_u = (u^2/2 (1 - th) g - u)/tau_u with g = u* - v^M,
+         * f_v = ((a - v) H(u - u_v) - v H(u_v - u))/tau_v with
+         * a = 1/(1 - e^-Re), differentiated term by term. */
+        double u = z[0], v = z[1], k = q[K_K], M = q[K_M];
+        double dth, th = karma_tanh(p, u, &dth);
+        double g = q[K_USTAR] - pow(v, M);
+        double a = 1.0 / (1.0 - exp(-q[K_RE]));
+        J[0] = (u * (1.0 - th) * g - u * u / 2.0 * dth * g - 1.0) / q[K_TU];
+        J[1] = -(u * u / 2.0) * (1.0 - th) * M * pow(v, M - 1.0) / q[K_TU];
+        J[2] = ((a - v) * orc_dHk(u - q[K_UV], k) + v * orc_dHk(q[K_UV] - u, k)) / q[K_TV];
+        J[3] = (-orc_Hk(u - q[K_UV], k) - orc_Hk(q[K_UV] - u, k)) / q[K_TV];
         return;
     }
     double u = z[0], v = z[1], w = z[2], s = z[3];
