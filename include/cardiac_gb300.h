@@ -57,9 +57,11 @@ typedef enum cg_status {
     CG_EUNSUPPORTED = 7     /* valid request this build does not implement */
 } cg_status;
 
-/* Models (Sect. 2).  CG_DIFFUSION is the linear case N = 0 with one field,
- * useful for checking the stencil and integrators against closed forms.
- * CG_KARMA is reserved: its constants are not printed in the paper. */
+/* Models (Sect. 2): FitzHugh-Nagumo (u, v both diffusive), Bueno-Orovio-
+ * Cherry-Fenton (u, v, w, s; u diffusive), the two-variable Karma model of
+ * Eq. (karma) (u, v; u diffusive with D_u = gamma).  CG_DIFFUSION is the
+ * linear case N = 0 with one field, useful for checking the stencil and
+ * integrators against closed forms. */
 enum { CG_FHN = 0, CG_BOCF = 1, CG_KARMA = 2, CG_DIFFUSION = 3 };
 /* Laplacian (Eq. diffusion): 5-point, or 9-point with diagonal weight alpha_d. */
 enum { CG_STENCIL5 = 0, CG_STENCIL9 = 1 };
@@ -85,7 +87,7 @@ enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2, CG_RUSH_LARSEN = 3, CG_IMPLICIT_EU
 #define CG_FLAG_NEIGHBOR_SYNC    (1u << 2)  /* static schedule only: between stages each block
                                                waits for the blocks that own its halo instead of
                                                a grid-wide barrier (an autotuner option) */
-#define CG_FLAG_TANH_AS_HK       (1u << 3)  /* four-field model only: the model variant of
+#define CG_FLAG_TANH_AS_HK       (1u << 3)  /* four-field and Karma models: the model variant of
                                                Sect. 6, each (1 + tanh(kk x))/2 replaced by the
                                                smoothed step H_{kk/3}(x) (same value and slope at
                                                x = 0).  Changes the model, not only its cost. */
@@ -143,7 +145,8 @@ typedef struct cg_plan_s *cg_plan;
 
 /* Validate a problem and build an immutable plan (coefficients, tile table,
  * launch shape).  Returns CG_EINVAL for a bad argument, CG_EUNSUPPORTED for a
- * gate integrator or CG_FLAG_TANH_AS_HK with a model other than CG_BOCF, and
+ * gate integrator with a model other than CG_BOCF or CG_FLAG_TANH_AS_HK with
+ * a model other than CG_BOCF and CG_KARMA, and
  * CG_EUNSTABLE when dt exceeds the linear bound 2/rho (Euler, Heun and the
  * u step of the gate integrators) or 2.785/rho (RK4), rho
  * the spectral radius of the diffusion operator, unless
@@ -355,15 +358,21 @@ cg_status cg_axpby(double a, const double *x, double b, double *y, int64_t n, vo
 /* Message describing the last error on the calling thread ("" if none). */
 const char *cg_last_error(void);
 
-/* Number of fields n_v of a model (2 FHN, 4 BOCF, 1 diffusion), -1 if unknown. */
+/* Number of fields n_v of a model (2 FHN, 4 BOCF, 2 Karma, 1 diffusion), -1
+ * if unknown. */
 int32_t cg_n_fields(int32_t model);
 
-/* Number of model constants (3 FHN: eps, a1, a0; 29 BOCF; 0 diffusion). */
+/* Number of model constants (3 FHN: eps, a1, a0; 29 BOCF; 8 Karma: tau_u,
+ * tau_v, u*, u_h, u_v, Re, M, k; 0 diffusion).  Karma: tau_u, tau_v and Re
+ * must be non-zero; an integer M in [0, 64] takes v^M by repeated squaring,
+ * any other M by pow(). */
 int32_t cg_n_params(int32_t model);
 
 /* Write the default constants of a model to out[0 .. cg_n_params(model)-1]
  * (host memory).  FHN: Sect. 2 values; BOCF: the epicardial set of the
- * model the paper cites, then k = 28.4 for H_k. */
+ * model the paper cites, then k = 28.4 for H_k; Karma: (Re, M) = (1, 6) and
+ * k = 28.4 of Sect. 2 with tau_u = 2.5, tau_v = 250, u* = 1.5415, u_h = 3,
+ * u_v = 1 of the model paper it cites (gamma = 0.0011 cm^2/ms is D_u). */
 cg_status cg_default_params(int32_t model, double *out);
 
 /* Host-only preview of the static schedule that plans use (no device

@@ -29,7 +29,7 @@ FLAG_TEST_STUCK_BARRIER = 1 << 8
 DEV_NONFINITE, DEV_TIMEOUT = 1, 2
 ABI_VERSION = 1
 
-_DEFAULT_D = {FHN: (1.0, 1.5), BOCF: (1.171e-3,), DIFFUSION: (1.0,)}
+_DEFAULT_D = {FHN: (1.0, 1.5), BOCF: (1.171e-3,), KARMA: (1.1e-3,), DIFFUSION: (1.0,)}
 
 
 def n_fields(model: int) -> int:

@@ -46,6 +46,7 @@ int n_fields(int model)
     switch (model) {
     case CG_FHN: return 2;
     case CG_BOCF: return 4;
+    case CG_KARMA: return 2;
     case CG_DIFFUSION: return 1;
     default: return -1;
     }
@@ -56,6 +57,7 @@ int n_diffusive(int model)
     switch (model) {
     case CG_FHN: return 2;
     case CG_BOCF: return 1;
+    case CG_KARMA: return 1;
     case CG_DIFFUSION: return 1;
     default: return 0;
     }
@@ -66,6 +68,7 @@ int n_params(int model)
     switch (model) {
     case CG_FHN: return 3;
     case CG_BOCF: return 29;
+    case CG_KARMA: return 8;
     case CG_DIFFUSION: return 0;
     default: return -1;
     }
@@ -93,7 +96,9 @@ int kernel_model(int model, uint32_t flags)
 // Default constants.  FHN: (eps, a1, a0) of Sect. 2.  BOCF: epicardial set
 // of the minimal model cited in Sect. 2 (order: uo uu thv thw thvm tho tv1m
 // tv2m tvp tw1m tw2m kwm uwm twp tfi to1 to2 tso1 tso2 kso uso ts1 ts2 ks us
-// tsi twinf winfstar), then the H_k sharpness k = 28.4 of Sect. 2.
+// tsi twinf winfstar), then the H_k sharpness k = 28.4 of Sect. 2.  Karma
+// (order tau_u tau_v u* u_h u_v Re M k): (Re, M) = (1, 6) and k = 28.4 of
+// Sect. 2, the others the values of the model paper it cites.
 void default_params(int model, double *out)
 {
     if (model == CG_FHN) {
@@ -104,6 +109,9 @@ void default_params(int model, double *out)
                               1.4506, 60.0,   15.0,    65.0,   0.03,   200.0, 0.11, 400.0,
                               6.0,    30.0181, 0.9957, 2.0458, 0.65,   2.7342, 16.0, 2.0994,
                               0.9087, 1.8875, 0.07,    0.94,   28.4};
+        std::memcpy(out, p, sizeof p);
+    } else if (model == CG_KARMA) {
+        const double p[8] = {2.5, 250.0, 1.5415, 3.0, 1.0, 1.0, 6.0, 28.4};
         std::memcpy(out, p, sizeof p);
     }
 }
@@ -165,6 +173,7 @@ const void *lookup_tb_kernel(int kmodel, int stencil, int scheme)
     case CG_FHN: return cgk::tb_kernel_fhn(stencil, scheme);
     case CG_BOCF: return cgk::tb_kernel_bocf(stencil, scheme);
     case CG_DIFFUSION: return cgk::tb_kernel_diff(stencil, scheme);
+    case CG_KARMA: return cgk::tb_kernel_karma(stencil, scheme);
     case cgk::MODEL_BOCFH: return cgk::tb_kernel_bocfh(stencil, scheme);
     default: return nullptr;
     }
@@ -176,6 +185,7 @@ const void *lookup_kernel(int kmodel, int stencil, int scheme, int cx)
     case CG_FHN: return cgk::fwd_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::fwd_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::fwd_kernel_diff(stencil, scheme, cx);
+    case CG_KARMA: return cgk::fwd_kernel_karma(stencil, scheme, cx);
     case cgk::MODEL_BOCFH: return cgk::fwd_kernel_bocfh(stencil, scheme, cx);
     default: return nullptr;
     }
@@ -211,9 +221,6 @@ cg_status validate(const cg_problem *p, int idx)
     if (p->abi_version != CG_ABI_VERSION)
         return fail(CG_EINVAL, "problem %d: abi_version %d, library speaks %d", idx, p->abi_version,
                     CG_ABI_VERSION);
-    if (p->model == CG_KARMA)
-        return fail(CG_EUNSUPPORTED, "problem %d: the Karma model's constants are not in the paper; "
-                                     "model not built", idx);
     const int nv = n_fields(p->model);
     if (nv < 0) return fail(CG_EINVAL, "problem %d: unknown model %d", idx, p->model);
     if (p->nx < 2 || p->ny < 2 || p->nx > (1 << 28) || p->ny > (1 << 28))
@@ -235,8 +242,9 @@ cg_status validate(const cg_problem *p, int idx)
     if (gate_scheme(p->scheme) && p->model != CG_BOCF)
         return fail(CG_EUNSUPPORTED, "problem %d: Rush-Larsen and implicit Euler integrate the gates of the "
                                      "four-field model only", idx);
-    if ((p->flags & CG_FLAG_TANH_AS_HK) && p->model != CG_BOCF)
-        return fail(CG_EUNSUPPORTED, "problem %d: CG_FLAG_TANH_AS_HK applies to the four-field model only", idx);
+    if ((p->flags & CG_FLAG_TANH_AS_HK) && p->model != CG_BOCF && p->model != CG_KARMA)
+        return fail(CG_EUNSUPPORTED, "problem %d: CG_FLAG_TANH_AS_HK applies to the four-field and Karma models "
+                                     "only", idx);
     if (gate_scheme(p->scheme) && p->params) {
         // the gate coefficients al are negative when these time constants are
         // positive: tv1m tv2m tvp tw1m tw2m twp ts1 ts2
@@ -259,6 +267,11 @@ cg_status validate(const cg_problem *p, int idx)
     if (p->params)
         for (int i = 0; i < p->n_params; ++i)
             if (!finite(p->params[i])) return fail(CG_EINVAL, "problem %d: param %d not finite", idx, i);
+    if (p->model == CG_KARMA && p->params) {
+        // tau_u, tau_v divide; Re = 0 makes 1/(1 - e^-Re) infinite
+        if (p->params[0] == 0 || p->params[1] == 0 || p->params[5] == 0)
+            return fail(CG_EINVAL, "problem %d: Karma tau_u, tau_v and Re must be non-zero", idx);
+    }
     if (!(p->flags & CG_FLAG_ALLOW_UNSTABLE)) {
         const double bound = (p->scheme == CG_RK4) ? 2.785 : 2.0;
         double rho = 0;
@@ -290,6 +303,24 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         I.mi[1] = I.wc[1] - eps * a1;
     } else if (p.model == CG_DIFFUSION) {
         I.mi[0] = I.wc[0];
+    } else if (p.model == CG_KARMA) {  // layout of cg_stepper.cuh
+        const double tu = prm[0], tv = prm[1], ustar = prm[2], uh = prm[3], uv = prm[4], re = prm[5], M = prm[6],
+                     k = prm[7];
+        const double a = 1.0 / (1.0 - std::exp(-re));
+        P.mp[cgk::KP_ITU] = 1.0 / tu;
+        P.mp[cgk::KP_ITV] = 1.0 / tv;
+        P.mp[cgk::KP_USTAR] = ustar;
+        P.mp[cgk::KP_SA] = 2.0 * uh;
+        P.mp[cgk::KP_HA] = 0.5 + uh / 3.0;
+        P.mp[cgk::KP_AITV] = a / tv;
+        P.mp[cgk::KP_K] = k;
+        P.mp[cgk::KP_CV] = 0.5 - k * uv;
+        P.mp[cgk::KP_6KA] = 6.0 * k * a / tv;
+        P.mp[cgk::KP_M] = M;
+        P.mp[cgk::KP_MI] = (M >= 0 && M <= 64 && M == std::floor(M)) ? M : -1.0;
+        P.mp[cgk::KP_TH] = (p.flags & CG_FLAG_TANH_AS_HK) ? 1.0 : 0.0;
+        static_assert(cgk::KP_N <= cgk::NMP, "model constant table too small");
+        I.mi[0] = I.wc[0] - 1.0 / tu;
     } else {  // BOCF, layout of cg_stepper.cuh
         for (int i = 0; i < 29; ++i) P.mp[i] = prm[i];
         const double k = prm[28];
@@ -1138,7 +1169,22 @@ const void *lookup_tlm_kernel(int kmodel, int stencil, int scheme, int cx)
     case CG_FHN: return cgk::tlm_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::tlm_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::tlm_kernel_diff(stencil, scheme, cx);
+    case CG_KARMA: return cgk::tlm_kernel_karma(stencil, scheme, cx);
     default: return nullptr;
+    }
+}
+
+// Stored Jacobian entries per cell of a kernel family (the models' own NJ;
+// 0 for the linear model).
+int model_nj(int kmodel)
+{
+    switch (kmodel) {
+    case CG_FHN: return cgk::Model<cgk::MODEL_FHN>::NJ;
+    case CG_BOCF: return cgk::Model<cgk::MODEL_BOCF>::NJ;
+    case cgk::MODEL_BOCFH: return cgk::Model<cgk::MODEL_BOCFH>::NJ;
+    case CG_KARMA: return cgk::Model<cgk::MODEL_KARMA>::NJ;
+    case CG_DIFFUSION: return cgk::Model<cgk::MODEL_DIFF>::NJ;
+    default: return 0;
     }
 }
 
@@ -1156,7 +1202,7 @@ TlmLayout tlm_layout(cg_plan P, int32_t n_tan, int64_t n_jstages = 1)
     TlmLayout L;
     L.tstride = (int64_t)P->nv * plane;
     L.tblk = round32((int64_t)cgk::SCRATCH_PLANES * P->nv * plane);
-    L.jstride = round32(std::max(1, cgk::model_nj(P->model)) * plane);
+    L.jstride = round32(std::max(1, model_nj(P->kmodel)) * plane);
     L.jbuf_off = cgk::WS_HEADER + (size_t)P->scratch_elems * sizeof(double);
     L.tan_off = L.jbuf_off + (size_t)std::max<int64_t>(1, n_jstages) * (size_t)L.jstride * sizeof(double);
     L.total = L.tan_off + (size_t)n_tan * (size_t)L.tblk * sizeof(double);
@@ -1344,6 +1390,7 @@ const void *lookup_adj_kernel(int kmodel, int stencil, int scheme, int cx)
     case CG_FHN: return cgk::adj_kernel_fhn(stencil, scheme, cx);
     case CG_BOCF: return cgk::adj_kernel_bocf(stencil, scheme, cx);
     case CG_DIFFUSION: return cgk::adj_kernel_diff(stencil, scheme, cx);
+    case CG_KARMA: return cgk::adj_kernel_karma(stencil, scheme, cx);
     default: return nullptr;
     }
 }

@@ -89,7 +89,7 @@ enum { SYNC_GRID = 0, SYNC_NEIGHBOR = 1 };
 
 // MODEL_BOCFH: the four-field model with its tanh terms replaced by smoothed
 // steps (CG_FLAG_TANH_AS_HK); an internal kernel family, not an ABI model id.
-enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_DIFF = CG_DIFFUSION, MODEL_BOCFH = 5 };
+enum { MODEL_FHN = CG_FHN, MODEL_BOCF = CG_BOCF, MODEL_KARMA = CG_KARMA, MODEL_DIFF = CG_DIFFUSION, MODEL_BOCFH = 5 };
 
 // Kernel lookup, one function per model translation unit.  Returns nullptr
 // for an unsupported combination.
@@ -109,6 +109,10 @@ const void *tlm_kernel_diff(int stencil, int scheme, int cx);
 const void *adj_kernel_fhn(int stencil, int scheme, int cx);
 const void *adj_kernel_bocf(int stencil, int scheme, int cx);
 const void *adj_kernel_diff(int stencil, int scheme, int cx);
+const void *fwd_kernel_karma(int stencil, int scheme, int cx);
+const void *tb_kernel_karma(int stencil, int scheme);
+const void *tlm_kernel_karma(int stencil, int scheme, int cx);
+const void *adj_kernel_karma(int stencil, int scheme, int cx);
 
 // Host: the four-field model's s-gate rates 1/ts1 and 1/(ts1 + dts) as the
 // kernels' own reciprocal computes them (out[0], out[1]); runs one tiny
@@ -121,11 +125,5 @@ void exp_table(double *tab, int n);
 
 // Record a message for cg_last_error() on the calling thread; returns st.
 cg_status set_last_error(cg_status st, const char *msg);
-
-// Stored Jacobian entries per cell of each model (0 for the linear model).
-inline int model_nj(int model)
-{
-    return model == CG_FHN ? 1 : model == CG_BOCF ? 10 : 0;
-}
 
 }  // namespace cgk

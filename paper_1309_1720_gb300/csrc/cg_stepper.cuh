@@ -234,6 +234,129 @@ template <> struct Model<MODEL_DIFF> {
     }
 };
 
+// Two-variable Karma model, Eq. (karma); only u diffuses (gamma = D_u).
+// With sig = (1 - tanh(u - u_h))/2 = sigmoid(2 (u_h - u)) and g = u* - v^M:
+//   t_u = wc_u u + (u^2 sig g - u)/tau_u     (u^2/2 (1 - tanh) = u^2 sig)
+//   t_v = (a H_k(u - u_v) - v)/tau_v         (H_k(u_v - u) = 1 - H_k(u - u_v)
+//                                             for the cubic step), a = 1/(1 - e^-Re)
+// Under the tanh variant of Sect. 6 (tanh x -> 2 H_{1/3}(x) - 1), sig is
+// H_{1/3}(u_h - u).  An integer M takes v^M by repeated squaring (the
+// integer power Sect. 6 recommends), any other M by pow().
+// Constant layout of mp (filled by the host):
+enum {
+    KP_ITU,     // 1/tau_u
+    KP_ITV,     // 1/tau_v
+    KP_USTAR,   // u*
+    KP_SA,      // 2 u_h: sig = sigmoid(2 u_h - 2 u)
+    KP_HA,      // 1/2 + u_h/3: variant sig = H(t), t = 1/2 + (u_h - u)/3
+    KP_AITV,    // a/tau_v
+    KP_K,       // k of H_k
+    KP_CV,      // 1/2 - k u_v
+    KP_6KA,     // 6 k a/tau_v: d t_v/du = KP_6KA t (1 - t)
+    KP_M,       // M
+    KP_MI,      // M if it is an integer in [0, 64], else -1
+    KP_TH,      // 1: tanh variant
+    KP_N
+};
+
+// v^m for an integer m >= 1 by repeated squaring.
+__device__ __forceinline__ double int_pow(double v, int m)
+{
+    double r = v;
+    m -= 1;
+    while (m > 0) {
+        if (m & 1) r *= v;
+        m >>= 1;
+        if (m) v *= v;
+    }
+    return r;
+}
+
+template <> struct Model<MODEL_KARMA> {
+    static constexpr int NV = 2, ND = 1;
+    // Stored Jacobian entries: [d t_u/du (wc_u folded in), d t_u/dv,
+    // d t_v/du]; d t_v/dv = -1/tau_v is a constant.
+    static constexpr int NJ = 3;
+    struct Coef { double A_u; const double *tab; };    // A_u = wc_u - 1/tau_u
+    __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.tab}; }
+
+    // v^M and, when JAC, M v^(M-1) (M = 0: 1 and 0).
+    template <bool JAC>
+    __device__ __forceinline__ static double vpow(const double *mp, double v, double &dvm)
+    {
+        const int mi = (int)mp[KP_MI];
+        if (mi >= 2) {
+            const double p1 = int_pow(v, mi - 1);
+            if constexpr (JAC) dvm = mp[KP_M] * p1;
+            return p1 * v;
+        }
+        if (mi == 1) {
+            if constexpr (JAC) dvm = 1.0;
+            return v;
+        }
+        if (mi == 0) {
+            if constexpr (JAC) dvm = 0.0;
+            return 1.0;
+        }
+        if constexpr (JAC) dvm = mp[KP_M] * pow(v, mp[KP_M] - 1.0);
+        return pow(v, mp[KP_M]);
+    }
+
+    template <bool JAC>
+    __device__ __forceinline__ static void eval(const Coef &c, const double *mp, const double (&z)[NV],
+                                                double (&t)[NV], double *J)
+    {
+        const double u = z[0], v = z[1];
+        double sig, dsig = 0.0;
+        if (mp[KP_TH] != 0.0) {
+            const double th = clamp01_int(fma(-1.0 / 3.0, u, mp[KP_HA]));
+            sig = (th * th) * fma(-2.0, th, 3.0);
+            if constexpr (JAC) dsig = -2.0 * (th * (1.0 - th));
+        } else if constexpr (JAC) {
+            double ds;
+            sig = sigmoid(fma(-2.0, u, mp[KP_SA]), c.tab, ds);
+            dsig = -2.0 * ds;
+        } else {
+            sig = sigmoid(fma(-2.0, u, mp[KP_SA]), c.tab);
+        }
+        double dvm = 0.0;
+        const double g = mp[KP_USTAR] - vpow<JAC>(mp, v, dvm);
+        const double uu = u * u;
+        const double q = uu * sig;
+        t[0] = fma(q * g, mp[KP_ITU], c.A_u * u);
+        const double tv = clamp01_int(fma(mp[KP_K], u, mp[KP_CV]));
+        const double H = (tv * tv) * fma(-2.0, tv, 3.0);
+        t[1] = fma(mp[KP_AITV], H, -(v * mp[KP_ITV]));
+        if constexpr (JAC) {
+            // d/du (u^2 sig g)/tau_u = (2 u sig + u^2 dsig) g / tau_u
+            J[0] = fma(fma(2.0 * u, sig, uu * dsig) * g, mp[KP_ITU], c.A_u);
+            J[1] = -(q * dvm) * mp[KP_ITU];
+            J[2] = mp[KP_6KA] * (tv * (1.0 - tv));
+        }
+    }
+    __device__ static void local(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV])
+    {
+        eval<false>(c, mp, z, t, nullptr);
+    }
+    __device__ static void local_jac(const Coef &c, const double *mp, const double (&z)[NV], double (&t)[NV],
+                                     double (&J)[NJ])
+    {
+        eval<true>(c, mp, z, t, J);
+    }
+    __device__ static void tan_local(const Coef &, const double *mp, const double (&J)[NJ], const double (&d)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = fma(J[0], d[0], J[1] * d[1]);
+        t[1] = fma(J[2], d[0], -(mp[KP_ITV] * d[1]));
+    }
+    __device__ static void adj_local(const Coef &, const double *mp, const double (&J)[NJ], const double (&k)[NV],
+                                     double (&t)[NV])
+    {
+        t[0] = fma(J[0], k[0], J[2] * k[1]);
+        t[1] = fma(J[1], k[0], -(mp[KP_ITV] * k[1]));
+    }
+};
+
 // Bueno-Orovio-Cherry-Fenton, Eq. (bochfe) with the currents J_fi, J_so,
 // J_si, the alpha/beta gate form and the u-dependent time constants of the
 // cited minimal model; every step is the cubic H_k.  Only u diffuses.

@@ -37,6 +37,8 @@ FHN_V_REST = -0.37276438744049384
 FHN_DX = 0.04          # Sect. 2, FitzHugh-Nagumo spatial step
 BOCF_DX = 0.03         # Sect. 2, Bueno-Orovio spatial step [cm]
 BOCF_D = 1.171e-3      # Sect. 2, D = 1.171 cm^2/s expressed in cm^2/ms
+KARMA_DX = 0.0262      # Sect. 2, Karma spatial step [cm]
+KARMA_GAMMA = 1.1e-3   # Sect. 2, gamma = 0.0011 (cm^2/ms)
 
 
 def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
@@ -94,6 +96,25 @@ def fhn_broken_wave(nx: int, ny: int, width: int | None = None, seed: int = 0,
     z[0, :, :width] = 1.0
     z[1, : ny // 2, :] = 0.6
     z[0] += noise * uniform_pm1(seed, nx * ny).reshape(ny, nx)
+    return z
+
+
+def karma_broken_wave(nx: int, ny: int, width: int | None = None, seed: int = 0,
+                      noise: float = 1e-3) -> np.ndarray:
+    """Broken plane wave for the Karma model, shape ``[2, ny, nx]``.
+
+    u is excited (u = 3) in the ``width`` left columns and rests at 0
+    elsewhere; v is refractory (v = 1.2, so v^6 > u* blocks excitation) in
+    the lower half ``y < ny/2`` and 0 elsewhere.  Then ``u += noise *
+    U[0, 1)`` drawn in row-major (y, x) order from ``seed``.  ``width``
+    defaults to 10 columns per 128.
+    """
+    if width is None:
+        width = max(1, (10 * nx) // 128)
+    z = np.zeros((2, ny, nx), dtype=np.float64)
+    z[0, :, :width] = 3.0
+    z[1, : ny // 2, :] = 1.2
+    z[0] += noise * uniform01(seed, nx * ny).reshape(ny, nx)
     return z
 
 

@@ -6,7 +6,7 @@ import numpy as np
 
 import oracle as O
 
-_MODEL = {0: O.FHN, 1: O.BOCF, 3: O.DIFFUSION}
+_MODEL = {0: O.FHN, 1: O.BOCF, 2: O.KARMA, 3: O.DIFFUSION}
 
 
 def oracle_problem(p):

@@ -43,7 +43,7 @@ def test_abi_version(L):
 def test_default_params_match_oracle(L):
     import oracle as O
     from paper_1309_1720_gb300 import api
-    for m_abi, m_orc in [(api.FHN, O.FHN), (api.BOCF, O.BOCF)]:
+    for m_abi, m_orc in [(api.FHN, O.FHN), (api.BOCF, O.BOCF), (api.KARMA, O.KARMA)]:
         assert api.n_fields(m_abi) == O.n_fields(m_orc)
         assert np.array_equal(np.array(api.default_params(m_abi)), O.default_params(m_orc))
 
@@ -59,13 +59,16 @@ def _create(prob):
 @pytest.mark.parametrize("kw,status", [
     (dict(nx=1), 1), (dict(ny=0), 1), (dict(dx=0.0), 1), (dict(dt=-1.0), 1),
     (dict(stencil=7), 1), (dict(bc=5), 1), (dict(scheme=9), 1), (dict(model=42), 1),
-    (dict(model=2), 7),                     # Karma: constants not in the paper
+    (dict(model=2, dx=0.0262, dt=0.05, D=(1.1e-3, 1e-3)), 7),   # Karma: v does not diffuse
+    (dict(model=2, dx=0.0262, dt=0.05, scheme=3), 7),            # Karma: no gate integrators
+    (dict(model=2, dx=0.0262, dt=0.05, params=[2.5, 250, 1.5415, 3, 1, 0, 6, 28.4]), 1),  # Re = 0
+    (dict(model=2, dx=0.0262, dt=0.2), 4),  # FE bound h^2/(4 gamma) = 0.156 ms
     (dict(dt=3e-4), 4),                     # FE bound for FHN at dx=0.04 is 2.67e-4
     (dict(scheme=2, dt=5.6e-4), 4),         # RK4 5-point bound 3.71e-4
     (dict(stencil=1, alpha_d=0.4), 1),
     (dict(params=[0.05, 1.5]), 1),
     (dict(scheme=3), 7), (dict(scheme=4), 7),   # gate integrators: four-field model only
-    (dict(flags=1 << 3), 7),                # tanh variant: four-field model only
+    (dict(flags=1 << 3), 7),                # tanh variant: four-field and Karma models only
     (dict(bc=3), 1), (dict(scheme=5), 1),
 ])
 def test_validation_errors(L, kw, status):
