@@ -177,10 +177,28 @@ def cpu_baseline(seconds_target=12.0):
     t = time.perf_counter()
     O.step(p, z1, n)
     dt = time.perf_counter() - t
-    return {"value": NX * NY * n / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of the 1024x1024 9-point two-field workload, single-threaded C oracle "
-                      "(-O2 -ffp-contract=off), rate extrapolated to the full run" % n,
-            "seconds": dt}
+    out = {"value": NX * NY * n / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+           "sample": "%d RK4 steps of the 1024x1024 9-point two-field workload, single-threaded C oracle "
+                     "(-O2 -ffp-contract=off), rate extrapolated to the full run" % n,
+           "seconds": dt}
+    # every host core: one independent single-threaded copy of the same
+    # oracle per core on the same sample (ctypes releases the GIL during the
+    # call, so the copies run in parallel; the oracle itself is unchanged)
+    import threading
+    cores = os.cpu_count() or 1
+    m = max(2, n // 4)
+    copies = [z1.copy() for _ in range(cores)]
+    threads = [threading.Thread(target=O.step, args=(p, c, m)) for c in copies]
+    t = time.perf_counter()
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    dt_all = time.perf_counter() - t
+    out["all_cores"] = {"value": cores * NX * NY * m / dt_all / 1e9, "unit": "GCUPS", "cores": cores,
+                        "kind": "oracle, one independent single-threaded copy per core",
+                        "sample": "%d RK4 steps per copy of the same workload" % m, "seconds": dt_all}
+    return out
 
 
 def run_reference(args):
@@ -279,6 +297,20 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         rows[name] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "steps_timed": steps,
                       "note": "launch shape of the RK4 row"}
         plan.close()
+
+    # the Karma model (Eq. karma): the 256^2 grid of the paper's timing
+    # figures (autotuned, temporal blocking allowed) and a 2048^2 grid
+    for n, steps in ((256, 2000), (2048, 500)):
+        p = api.Problem(model=api.KARMA, nx=n, ny=n, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,), scheme=api.RK4,
+                        dt=0.05)
+        z = torch.from_numpy(I.karma_broken_wave(n, n, seed=0)).cuda()
+        tun = autotune.tune([p], z, n_steps=200 if n <= 256 else 10)
+        plan = autotune.plan_for([p], tun)
+        t = timed(plan, z, steps, reps=2)
+        rows["karma-%dx%d-5pt-rk4" % (n, n)] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "tuning": tun,
+                                               "steps_timed": steps, "us_per_step": 1e6 * t / steps}
+        plan.close()
+        del z
 
     # 256 uneven instances (64..512, seed 1), 5-point RK4: one persistent
     # launch replayed from a CUDA graph vs 256 sequential single-instance runs
@@ -430,7 +462,7 @@ def _fit_slope(xs, ys):
 
 def paper_experiments(which):
     """The measurements of the paper's Sect. 5 on the GB300 stepper, for the
-    two models built here: wall time per unit of simulated time against dt
+    three models of Sect. 2: wall time per unit of simulated time against dt
     (Fig. 3), against the grid size N (Fig. 4, with the crossover N0 of the
     fit tau = a max(1, b N^2)), relative L2 accuracy against dt with the
     observed orders (Fig. 5, Table 2), and cost against accuracy (Fig. 6).
@@ -463,6 +495,10 @@ def paper_experiments(which):
                      dts=[0.1, 0.05, 0.025, 0.0125, 0.00625],
                      schemes=[api.EULER, api.RUSH_LARSEN, api.IMPLICIT_EULER, api.HEUN, api.RK4],
                      ic=lambda n: I.bocf_spiral_cores(n, n, seed=0)),
+        "karma": dict(prob=dict(model=api.KARMA, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,)), T=10.0,
+                      dts=[0.1, 0.05, 0.025, 0.0125, 0.00625],
+                      schemes=[api.EULER, api.HEUN, api.RK4],
+                      ic=lambda n: I.karma_broken_wave(n, n, seed=0)),
     }
     n = 256
     step_time = {}
@@ -485,15 +521,20 @@ def paper_experiments(which):
             print(json.dumps({"experiment": "timing_vs_dt (Fig. 3)", "grid": n, "steps_timed": 2000,
                               "tau": "device seconds per unit of simulated time = time per step / dt",
                               "results": res}), flush=True)
-    if which in ("all", "grid"):
+    grid_models = {
+        "fhn 5-point": (dict(model=api.FHN, dx=0.04), 1e-4, lambda N: I.fhn_broken_wave(N, N, seed=0)),
+        "karma 5-point": (dict(model=api.KARMA, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,)), 0.05,
+                          lambda N: I.karma_broken_wave(N, N, seed=0)),
+    }
+    for gname, (gprob, gdt, gic) in (grid_models.items() if which in ("all", "grid") else []):
         res = {}
         Ns = [32, 48, 64, 96, 128, 181, 256, 362, 512, 724, 1024, 1448, 2048, 2896, 4096]
         for sc in (api.EULER, api.HEUN, api.RK4):
             ts, tb = [], {}
             for N in Ns:
-                prob = api.Problem(model=api.FHN, nx=N, ny=N, dx=0.04, scheme=sc, dt=1e-4)
+                prob = api.Problem(nx=N, ny=N, scheme=sc, dt=gdt, **gprob)
                 plan = Plan(prob)
-                z = torch.from_numpy(I.fhn_broken_wave(N, N, seed=0)).cuda()
+                z = torch.from_numpy(gic(N)).cuda()
                 ts.append(timed_step(plan, z, 2000, reps=2) * 2000)
                 plan.close()
                 # temporally blocked (best of k = 2, 4, 8 steps per barrier) where it fits
@@ -520,7 +561,7 @@ def paper_experiments(which):
                               "gcups_at_4096": 4096 ** 2 * 2000 / ts[-1] / 1e9,
                               "temporal_blocking": tb, "a_s_temporal_blocking": a_tb,
                               "N0_temporal_blocking": (a_tb / b) ** 0.5}
-        print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": "fhn 5-point", "steps": 2000,
+        print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": gname, "steps": 2000,
                           "fit": "t = a max(1, (N/N0)^2), a = median of N <= 64, b = a/N0^2 = median t/N^2 "
                                  "for N >= 2048", "results": res}), flush=True)
     if which in ("all", "orbit"):

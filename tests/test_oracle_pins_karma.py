@@ -213,3 +213,29 @@ def test_adjoint_dD_fd():
     h = 1e-7
     fd = (L(g0 + h) - L(g0 - h)) / (2 * h)
     assert dLdD[0] == pytest.approx(fd, rel=1e-6)
+
+
+def test_rk4_order_and_the_smoothed_step():
+    """Table 2 reports order 3 instead of 4 for RK4 on the Karma and
+    Bueno-Orovio models, which the paper leaves unexplained.  Both models
+    switch through the cubic H_k, which is only C^1: its second derivative
+    jumps at k x = +-1/2.  On a gradient-free state (the model's ODE): while
+    u stays inside one smooth piece the observed order is 4; on a trajectory
+    whose u falls through the band edges of H_k(u - u_v) at the end of the
+    action potential it drops below 3.5 (a step that straddles an edge makes
+    a local error of order dt^3)."""
+    def run(z0, T, dt):
+        p = O.problem(O.KARMA, nx=3, ny=3, dx=0.0262, scheme=O.RK4, dt=dt)
+        return O.step(p, _uniform(z0[0], z0[1], 3, 3), int(round(T / dt)))[:, 0, 0]
+
+    dts = [0.1, 0.05, 0.025, 0.0125, 0.00625]
+    smooth = ((1.02, 0.3), 10.0)             # upstroke away from the band edges
+    ref = run(*smooth, dts[-1] / 16)
+    errs = [np.linalg.norm(run(*smooth, d) - ref) for d in dts[:3]]
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(slopes) > 3.9, slopes
+    across = ((3.5, 1.02), 60.0)             # plateau, recovery through u = u_v
+    ref = run(*across, dts[-1] / 16)
+    errs = [np.linalg.norm(run(*across, d) - ref) for d in dts]
+    fit = np.polyfit(np.log(dts), np.log(errs), 1)[0]
+    assert 2.0 < fit < 3.5, fit
