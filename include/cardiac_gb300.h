@@ -54,7 +54,8 @@ typedef enum cg_status {
     CG_EUNSTABLE = 4,       /* dt above the scheme's linear diffusive stability bound */
     CG_ENAN = 5,            /* a non-finite value was written (device status) */
     CG_ETIMEOUT = 6,        /* a bounded device wait gave up (device status) */
-    CG_EUNSUPPORTED = 7     /* valid request this build does not implement */
+    CG_EUNSUPPORTED = 7,    /* valid request this build does not implement */
+    CG_EBOUNDS = 8          /* checked build: a device-side index check failed (device status) */
 } cg_status;
 
 /* Models (Sect. 2): FitzHugh-Nagumo (u, v both diffusive), Bueno-Orovio-
@@ -99,6 +100,9 @@ enum { CG_EULER = 0, CG_HEUN = 1, CG_RK4 = 2, CG_RUSH_LARSEN = 3, CG_IMPLICIT_EU
 /* Device status bits (cg_read_status). */
 #define CG_DEV_NONFINITE 1u   /* a non-finite value was stored */
 #define CG_DEV_TIMEOUT   2u   /* a grid barrier wait gave up */
+#define CG_DEV_BOUNDS    4u   /* checked build only: a stage worker found an index outside the
+                                 grid (or its shared-memory window) before using it and skipped
+                                 the access */
 
 typedef struct cg_problem {
     int32_t abi_version;   /* must be CG_ABI_VERSION */
@@ -247,8 +251,9 @@ cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_out_host,
                       void *workspace, void *stream);
 
 /* Synchronise the stream and return the device status bits (CG_DEV_*)
- * recorded by the last run that used this workspace.  Returns CG_ENAN or
- * CG_ETIMEOUT when the matching bit is set, CG_OK otherwise. */
+ * recorded by the last run that used this workspace.  Returns CG_EBOUNDS,
+ * CG_ETIMEOUT or CG_ENAN when the matching bit is set (in that order of
+ * precedence), CG_OK otherwise. */
 cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags);
 
 /* ------------------------------------------------- tangent-linear model */
@@ -394,6 +399,14 @@ cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_ins
 
 /* CG_ABI_VERSION of the loaded library. */
 int32_t cg_abi_version(void);
+
+/* 1 for the checked build (libcardiac_gb300_checked.so, compiled with
+ * CG_BOUNDS_CHECK): every stage worker of the forward, tangent-linear,
+ * adjoint and temporally blocked kernels checks the grid and window indices
+ * it is about to use, skips an access that would leave them and reports
+ * CG_DEV_BOUNDS; results are otherwise bit for bit those of the plain build.
+ * 0 for the plain build. */
+int32_t cg_bounds_checked(void);
 
 #ifdef __cplusplus
 }

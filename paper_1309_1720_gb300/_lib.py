@@ -10,7 +10,10 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcardiac_gb300.so")
+# CG_BOUNDS_CHECK=1 in the environment loads the checked build instead (every
+# stage worker checks its indices before use; see cg_bounds_checked).
+CHECKED = os.environ.get("CG_BOUNDS_CHECK", "") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libcardiac_gb300_checked.so" if CHECKED else "libcardiac_gb300.so")
 
 c_dp = ctypes.POINTER(ctypes.c_double)
 
@@ -99,6 +102,7 @@ _SIGS = {
     "cg_n_params": (ctypes.c_int32, [ctypes.c_int32]),
     "cg_default_params": (ctypes.c_int, [ctypes.c_int32, c_dp]),
     "cg_abi_version": (ctypes.c_int32, []),
+    "cg_bounds_checked": (ctypes.c_int32, []),
     "cg_static_schedule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
@@ -118,8 +122,7 @@ def lib() -> ctypes.CDLL:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise ImportError(
-                    "libcardiac_gb300.so is not built (expected at %s); run "
-                    "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+                    "%s is not built; run `python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
             L = ctypes.CDLL(LIB_PATH)
             for name, (res, args) in _SIGS.items():
                 fn = getattr(L, name)

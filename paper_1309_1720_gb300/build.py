@@ -2,6 +2,8 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel, then linked into
 one shared library next to this file.  Rebuilds only what changed.
+``build(checked=True)`` makes libcardiac_gb300_checked.so from the same
+sources with -DCG_BOUNDS_CHECK (index checks in every stage worker).
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcardiac_gb300.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libcardiac_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,15 +49,16 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(h) for h in hdrs)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
+    bdir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     dep_t = _deps_mtime()
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(bdir, os.path.basename(s)[:-3] + ".o")
         if force or ptxas_info or not os.path.exists(o) or os.path.getmtime(o) < max(dep_t, os.path.getmtime(s)):
-            extra = ["-Xptxas", "-v"] if ptxas_info else []
+            extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DCG_BOUNDS_CHECK"] if checked else [])
             jobs.append((s, o, [nvcc()] + _flags(extra) + ["-c", s, "-o", o]))
 
     def run(job):
@@ -68,17 +73,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             for s, err in ex.map(run, jobs):
                 if verbose or ptxas_info:
                     sys.stderr.write("== %s\n%s" % (os.path.basename(s), err))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    if force or jobs or not os.path.exists(lib_path):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -111,6 +111,13 @@ struct Adjoint {
             return CX == 2 && I.vec_ok != 0 && full && ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
         };
         const bool vk = vec_for(Kin) && vec_for(Kout), vy = vec_for(Y), vl = vec_for(lam) && vec_for(lacc);
+        if constexpr (BOUNDS_CHECK) {
+            const bool rows = row_out_of_grid(sg.y0, ny) || row_out_of_grid(sg.y1, ny) || sg.y1 < sg.y0 ||
+                              row_out_of_grid(map_idx(sg.y0 - 1, ny, bc), ny) || bad_ptr(Y) || bad_ptr(Kin) ||
+                              bad_ptr(Kout) || bad_ptr(lam) || bad_ptr(lacc);
+            if (cols_out_of_grid<CX>(cx, hx, want_halo, x0, nx, I.vec_ok != 0 && full) || rows)
+                return CG_DEV_BOUNDS;
+        }
 
         // W^-1 factors of this lane's columns and halo column; W of its cells
         double fx[CX], wcol[CX];
@@ -151,6 +158,9 @@ struct Adjoint {
         uint32_t bad = 0;
         for (int y = sg.y0; y <= sg.y1; ++y) {
             const int yn = map_idx(y + 1, ny, bc);
+            if constexpr (BOUNDS_CHECK) {
+                if (row_out_of_grid(yn, ny)) return bad | CG_DEV_BOUNDS;
+            }
 #pragma unroll
             for (int f = 0; f < ND; ++f)
                 load_scaled<BND>(Kin + f * plane, nx, ny, yn, cx, hx, vk, want_halo, mirror, xedge, fx, fh, hi[f],
@@ -323,8 +333,8 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CG_FULL, v, o);
         if (lane == 0) b.partial[(int64_t)gw * ND + f] += v;
     }
-    bad = __any_sync(CG_FULL, bad != 0);
-    if (lane == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+    bad = __reduce_or_sync(CG_FULL, bad);
+    if (lane == 0 && bad) atomicOr(a.status, bad);
 }
 
 // dst[i] = c * src[i]

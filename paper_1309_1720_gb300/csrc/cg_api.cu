@@ -1153,6 +1153,7 @@ CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *strea
                    cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
     *flags = v;
+    if (v & CG_DEV_BOUNDS) return fail(CG_EBOUNDS, "a device-side index check failed (status 0x%x)", v);
     if (v & CG_DEV_TIMEOUT) return fail(CG_ETIMEOUT, "a device-side wait gave up (status 0x%x)", v);
     if (v & CG_DEV_NONFINITE) return fail(CG_ENAN, "a non-finite value was written (status 0x%x)", v);
     return CG_OK;
@@ -1586,4 +1587,9 @@ CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_
 CG_API int32_t cg_abi_version(void)
 {
     return CG_ABI_VERSION;
+}
+
+CG_API int32_t cg_bounds_checked(void)
+{
+    return cgk::BOUNDS_CHECK ? 1 : 0;
 }

@@ -161,6 +161,41 @@ __device__ __forceinline__ bool stage_sync(const RunArgs &a, int64_t g, bool fir
     return grid_barrier(reinterpret_cast<unsigned long long *>(a.sync), a.status, a.timeout_ns, target);
 }
 
+// ----------------------------------------------------------- checked build
+// Compiled with -DCG_BOUNDS_CHECK (libcardiac_gb300_checked.so), every stage
+// worker checks the indices it is about to use before the first access of a
+// segment (each lane's columns and halo column, the vector-access
+// conditions, the buffer pointers) and before each new row; a failed check
+// skips the rest of the segment and sets CG_DEV_BOUNDS in the status word.
+// Only integer compares are added, so results equal the plain build's bit
+// for bit.  It stands in for a memory checker, which is not available here.
+#ifdef CG_BOUNDS_CHECK
+constexpr bool BOUNDS_CHECK = true;
+#else
+constexpr bool BOUNDS_CHECK = false;
+#endif
+
+// Warp-uniform: some lane's column or halo column lies outside [0, nx), or a
+// 16-byte access would not cover two adjacent cells starting at an even one.
+template <int CX>
+__device__ __forceinline__ bool cols_out_of_grid(const int (&cx)[CX], int hx, bool want_halo, int x0, int nx,
+                                                 bool vec_row)
+{
+    bool b = x0 < 0;
+#pragma unroll
+    for (int c = 0; c < CX; ++c) b |= (cx[c] < 0) || (cx[c] >= nx);
+    b |= want_halo && ((hx < 0) || (hx >= nx));
+    if (CX == 2 && vec_row) b |= ((cx[0] & 1) != 0) || (cx[CX - 1] != cx[0] + 1) || (x0 + CX > nx);
+    return __any_sync(CG_FULL, b);
+}
+
+__device__ __forceinline__ bool row_out_of_grid(int y, int ny) { return y < 0 || y >= ny; }
+
+__device__ __forceinline__ bool bad_ptr(const void *p)
+{
+    return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 7) != 0;
+}
+
 // ------------------------------------------------------------------ models
 
 template <int M> struct Model;
@@ -857,6 +892,14 @@ struct Stepper {
         };
         const bool vin = vec_for(Yin), vsrc = vec_for(src), vacc = vec_for(acc);
         const bool vdst = vec_for(dst), vyn = vec_for(Ynext);
+        if constexpr (BOUNDS_CHECK) {
+            const bool vec_row = aligned_base && full;
+            bool rows = row_out_of_grid(y0, ny) || row_out_of_grid(y1, ny) || y1 < y0 ||
+                        row_out_of_grid(map_idx(y0 - 1, ny, bc), ny);
+            rows = rows || bad_ptr(Yin) || bad_ptr(src) || bad_ptr(dst) || bad_ptr(acc) || bad_ptr(Ynext);
+            if constexpr (KIND != KIND_PRIMAL) rows = rows || bad_ptr(jbuf);
+            if (cols_out_of_grid<CX>(cx, hx, want_halo, x0, nx, vec_row) || rows) return CG_DEV_BOUNDS;
+        }
 
         // stencil weights of the diffusive fields
         double wx[ND], wy[ND], wd[ND], wt[ND];
@@ -891,6 +934,9 @@ struct Stepper {
         uint32_t bad = 0;
         for (int y = y0; y <= y1; ++y) {
             const int yn = map_idx(y + 1, ny, bc);
+            if constexpr (BOUNDS_CHECK) {
+                if (row_out_of_grid(yn, ny)) return bad | CG_DEV_BOUNDS;
+            }
 #pragma unroll
             for (int f = 0; f < ND; ++f)
                 load_row(Yin + f * plane, nx, yn, cx, hx, vin, want_halo, hi[f], hhi[f]);
@@ -1170,8 +1216,8 @@ __global__ void __launch_bounds__(512, 1) k_stage(const RunArgs a)
             }
         }
     }
-    bad = __any_sync(CG_FULL, bad != 0);
-    if (lane == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+    bad = __reduce_or_sync(CG_FULL, bad);
+    if (lane == 0 && bad) atomicOr(a.status, bad);
 }
 
 // Kernel table for one model: [stencil][scheme][cx-1].

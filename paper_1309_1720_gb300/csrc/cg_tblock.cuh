@@ -81,6 +81,11 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     double *YB = YA + NV * WS;
     if (NS == 1) Z = YA;
     auto at = [&](int gx, int gy) { return (gy - gy0) * WX + (gx - gx0); };
+    // checked build: (gx, gy) is a window cell and the window fits the arrays
+    const bool win_fits = WX * (gy1 - gy0) <= WS;
+    auto in_window = [&](int gx, int gy) {
+        return win_fits && gx >= gx0 && gx < gx1 && gy >= gy0 && gy < gy1;
+    };
 
     double wx[ND > 0 ? ND : 1], wy[ND > 0 ? ND : 1], wd[ND > 0 ? ND : 1], wt[ND > 0 ? ND : 1];
 #pragma unroll
@@ -94,6 +99,7 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     const double *mp = a.mp;
     const int64_t plane = (int64_t)nx * ny;
 
+    uint32_t bad = 0;
     // Ghost points of buffer B on the region [xl, xh) x [yl, yh): x ghosts of
     // its rows first, then whole y-ghost rows (corners follow both flips).
     auto fill_ghosts = [&](double *B, int xl, int xh, int yl, int yh) {
@@ -106,6 +112,12 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             const int y = yl + (q >> 1);
             const bool lft = (q & 1) == 0;
             if (lft ? !left : !right) continue;
+            if constexpr (BOUNDS_CHECK) {
+                if (!in_window(lft ? -1 : nx, y) || !in_window(lft ? gx_lo : gx_hi, y)) {
+                    bad |= CG_DEV_BOUNDS;
+                    continue;
+                }
+            }
             const int dst = at(lft ? -1 : nx, y), src = at(lft ? gx_lo : gx_hi, y);
 #pragma unroll
             for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
@@ -117,6 +129,12 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             const int x = cl + (q >> 1);
             const bool lo = (q & 1) == 0;
             if (lo ? !bot : !top) continue;
+            if constexpr (BOUNDS_CHECK) {
+                if (!in_window(x, lo ? -1 : ny) || !in_window(x, lo ? gy_lo : gy_hi)) {
+                    bad |= CG_DEV_BOUNDS;
+                    continue;
+                }
+            }
             const int dst = at(x, lo ? -1 : ny), src = at(x, lo ? gy_lo : gy_hi);
 #pragma unroll
             for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
@@ -125,95 +143,124 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     };
 
     const int64_t P = (t.n_steps + t.k - 1) / t.k;
-    uint32_t bad = 0;
+    const bool tb_ok = !BOUNDS_CHECK || (win_fits && WX >= 3 && gy1 - gy0 >= 3);
+    if (!tb_ok) bad |= CG_DEV_BOUNDS;
     for (int64_t p = 0; p < P; ++p) {
         const int64_t rest = t.n_steps - p * t.k;
         const int kp = (int)(rest < t.k ? rest : t.k);
         const int H = kp * NS;
         const double *src = (p == 0) ? a.z_in : tb_dst(a, t, p - 1, P);
         double *dst = tb_dst(a, t, p, P);
-        // load the window's domain cells: the tile plus H cells of halo
-        {
-            const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
-            const int w = xh - xl, n = w * (yh - yl);
-            for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const int gx = xl + c % w, gy = yl + c / w;
-#pragma unroll
-                for (int f = 0; f < NV; ++f) Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
-            }
-            __syncthreads();
-            fill_ghosts(Z, xl, xh, yl, yh);
-        }
-        double *Yin = Z;
-        for (int g = 1; g <= H; ++g) {
-            const int s = (g - 1) % NS;
-            const bool last = (s == NS - 1);
-            const int rad = H - g;
-            const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
-            const int w = xh - xl, n = w * (yh - yl);
-            double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
-            const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
-            // every thread runs the same number of iterations, so the model's
-            // warp-uniform paths see whole warps; surplus threads repeat the
-            // last cell and store nothing
-            for (int base = 0; base < n; base += blockDim.x) {
-                const int c = base + (int)threadIdx.x;
-                const bool act = c < n;
-                const int cc = act ? c : n - 1;
-                const int gx = xl + cc % w, gy = yl + cc / w;
-                const int li = at(gx, gy);
-                double zc[NV];
-#pragma unroll
-                for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
-                double F[NV];
-                MD::local(coef, mp, zc, F);
-#pragma unroll
-                for (int f = 0; f < ND; ++f) {
-                    const double *Q = Yin + f * WS;
-                    const double Wv = Q[li - 1], Ev = Q[li + 1];
-                    if (ST == CG_STENCIL9) {
-                        const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
-                        const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
-                        const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
-                        const double acc_f = fma(wd[f], Tl + Th, F[f]);
-                        F[f] = fma(wx[f], Wv + Ev, acc_f);
-                    } else {
-                        double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
-                        F[f] = fma(wx[f], Wv + Ev, acc_f);
+        // checked build: a window that does not fit its arrays skips every
+        // access of this block (it still joins the grid barriers)
+        if (tb_ok) {
+            // load the window's domain cells: the tile plus H cells of halo
+            {
+                const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
+                const int w = xh - xl, n = w * (yh - yl);
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    const int gx = xl + c % w, gy = yl + c / w;
+                    if constexpr (BOUNDS_CHECK) {
+                        if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(src)) {
+                            bad |= CG_DEV_BOUNDS;
+                            continue;
+                        }
                     }
-                }
-                if (act) {
 #pragma unroll
-                    for (int f = 0; f < NV; ++f) {
-                        const int o = f * WS + li;
-                        if (NS == 1) {
-                            Yout[o] = fma(ca, F[f], zc[f]);
-                        } else if (s == 0) {
-                            ACC[o] = fma(ca, F[f], zc[f]);
-                            Yout[o] = fma(cyv, F[f], zc[f]);
-                        } else if (!last) {
-                            ACC[o] = fma(ca, F[f], ACC[o]);
-                            Yout[o] = fma(cyv, F[f], Z[o]);
+                    for (int f = 0; f < NV; ++f)
+                        Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
+                }
+                __syncthreads();
+                fill_ghosts(Z, xl, xh, yl, yh);
+            }
+            double *Yin = Z;
+            for (int g = 1; g <= H; ++g) {
+                const int s = (g - 1) % NS;
+                const bool last = (s == NS - 1);
+                const int rad = H - g;
+                const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
+                const int w = xh - xl, n = w * (yh - yl);
+                double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
+                const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
+                // every thread runs the same number of iterations, so the model's
+                // warp-uniform paths see whole warps; surplus threads repeat the
+                // last cell and store nothing
+                for (int base = 0; base < n; base += blockDim.x) {
+                    const int c = base + (int)threadIdx.x;
+                    const bool act = c < n;
+                    const int cc = act ? c : n - 1;
+                    const int gx = xl + cc % w, gy = yl + cc / w;
+                    int li = at(gx, gy);
+                    bool act_ok = act;
+                    if constexpr (BOUNDS_CHECK) {
+                        // the cell and its eight neighbours inside the window; a
+                        // failed check computes a harmless interior cell instead
+                        // and stores nothing (the model still sees whole warps)
+                        if (!(in_window(gx - 1, gy - 1) && in_window(gx + 1, gy + 1)) && n > 0) {
+                            bad |= CG_DEV_BOUNDS;
+                            li = WX + 1;
+                            act_ok = false;
+                        }
+                    }
+                    double zc[NV];
+#pragma unroll
+                    for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
+                    double F[NV];
+                    MD::local(coef, mp, zc, F);
+#pragma unroll
+                    for (int f = 0; f < ND; ++f) {
+                        const double *Q = Yin + f * WS;
+                        const double Wv = Q[li - 1], Ev = Q[li + 1];
+                        if (ST == CG_STENCIL9) {
+                            const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
+                            const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
+                            const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
+                            const double acc_f = fma(wd[f], Tl + Th, F[f]);
+                            F[f] = fma(wx[f], Wv + Ev, acc_f);
                         } else {
-                            Yout[o] = fma(ca, F[f], ACC[o]);
+                            double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
+                            F[f] = fma(wx[f], Wv + Ev, acc_f);
+                        }
+                    }
+                    if (act_ok) {
+#pragma unroll
+                        for (int f = 0; f < NV; ++f) {
+                            const int o = f * WS + li;
+                            if (NS == 1) {
+                                Yout[o] = fma(ca, F[f], zc[f]);
+                            } else if (s == 0) {
+                                ACC[o] = fma(ca, F[f], zc[f]);
+                                Yout[o] = fma(cyv, F[f], zc[f]);
+                            } else if (!last) {
+                                ACC[o] = fma(ca, F[f], ACC[o]);
+                                Yout[o] = fma(cyv, F[f], Z[o]);
+                            } else {
+                                Yout[o] = fma(ca, F[f], ACC[o]);
+                            }
                         }
                     }
                 }
+                __syncthreads();
+                fill_ghosts(Yout, xl, xh, yl, yh);
+                Yin = Yout;
             }
-            __syncthreads();
-            fill_ghosts(Yout, xl, xh, yl, yh);
-            Yin = Yout;
-        }
-        // write the tile back
-        {
-            const int w = x1 - x0, n = w * (y1 - y0);
-            for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const int gx = x0 + c % w, gy = y0 + c / w;
+            // write the tile back
+            {
+                const int w = x1 - x0, n = w * (y1 - y0);
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    const int gx = x0 + c % w, gy = y0 + c / w;
+                    if constexpr (BOUNDS_CHECK) {
+                        if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(dst)) {
+                            bad |= CG_DEV_BOUNDS;
+                            continue;
+                        }
+                    }
 #pragma unroll
-                for (int f = 0; f < NV; ++f) {
-                    const double v = Yin[f * WS + at(gx, gy)];
-                    bad |= nonfinite_bit(v);
-                    __stcg(dst + f * plane + (int64_t)gy * nx + gx, v);
+                    for (int f = 0; f < NV; ++f) {
+                        const double v = Yin[f * WS + at(gx, gy)];
+                        bad |= nonfinite_bit(v);
+                        __stcg(dst + f * plane + (int64_t)gy * nx + gx, v);
+                    }
                 }
             }
         }
@@ -224,8 +271,8 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
                 return;
         }
     }
-    bad = __any_sync(CG_FULL, bad != 0);
-    if ((threadIdx.x & 31) == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+    bad = __reduce_or_sync(CG_FULL, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(a.status, bad);
 }
 
 // Kernel table for one model: [stencil][scheme] (explicit schemes only).

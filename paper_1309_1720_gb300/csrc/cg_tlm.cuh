@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
             if (g + 1 < a.g_end && !stage_sync(a, g, g == a.g_begin)) return;
         }
     }
-    bad = __any_sync(CG_FULL, bad != 0);
-    if (lane == 0 && bad) atomicOr(a.status, CG_DEV_NONFINITE);
+    bad = __reduce_or_sync(CG_FULL, bad);
+    if (lane == 0 && bad) atomicOr(a.status, bad);
 }
 
 template <int M>

@@ -121,3 +121,22 @@ def test_linearized_tangent_entry_points_reject_null_plan(L):
     nit = ctypes.c_int32()
     assert L.cg_newton_gmres_step_linearized(None, None, 10, 30, 1, 1e-8, None, hist, ctypes.byref(nit),
                                              None, None) == 1
+
+
+def test_checked_build_loads_and_exports(L):
+    """The checked build (index checks in every stage worker) is a drop-in
+    replacement: same exported symbols, selected by CG_BOUNDS_CHECK=1."""
+    import subprocess
+    import sys
+    from paper_1309_1720_gb300 import build
+    build.build(checked=True)
+    assert L.cg_bounds_checked() == 0
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    chk.cg_bounds_checked.restype = ctypes.c_int32
+    assert chk.cg_bounds_checked() == 1
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+    code = ("from paper_1309_1720_gb300 import _lib; import sys; "
+            "sys.exit(0 if _lib.lib().cg_bounds_checked() == 1 else 3)")
+    env = dict(os.environ, CG_BOUNDS_CHECK="1")
+    assert subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env).returncode == 0
