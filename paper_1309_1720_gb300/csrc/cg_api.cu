@@ -805,12 +805,14 @@ CG_API cg_status cg_plan_create(const cg_problem *prob, cg_plan *out)
 
 CG_API cg_status cg_plan_create_tuned(const cg_problem *prob, const cg_tuning *tuning, cg_plan *out)
 {
+    cgk::NvtxRange nvtx_range("cg_plan_create");
     return make_plan(prob, 1, tuning, out);
 }
 
 CG_API cg_status cg_batch_create(const cg_problem *probs, int32_t n_inst, const cg_tuning *tuning,
                                  cg_plan *out)
 {
+    cgk::NvtxRange nvtx_range("cg_batch_create");
     return make_plan(probs, n_inst, tuning, out);
 }
 
@@ -1016,6 +1018,7 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
 CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps, void *workspace,
                         void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
     if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
@@ -1035,6 +1038,7 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
 CG_API cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *const *z_out, int64_t n_steps,
                               void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_batch_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
     if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
@@ -1054,6 +1058,7 @@ CG_API cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *c
 
 CG_API cg_status cg_rhs(cg_plan plan, const double *z, double *f, void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_rhs");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z || !f || !workspace) return fail(CG_EINVAL, "NULL buffer");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
@@ -1124,6 +1129,7 @@ CG_API cg_status cg_host_workspace_size(cg_plan plan, size_t *bytes)
 CG_API cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_out_host, int64_t n_steps,
                              void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_run_host");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in_host || !z_out_host || !workspace) return fail(CG_EINVAL, "NULL buffer");
     if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
@@ -1257,6 +1263,7 @@ CG_API cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t 
 CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, double *zT, double *dzT,
                             int32_t n_tangents, int64_t n_steps, void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_tlm_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
     if (gate_scheme(plan->scheme))
@@ -1371,12 +1378,14 @@ static cg_status tlm_linearized(cg_plan plan, const double *z0, double *zT, cons
 CG_API cg_status cg_tlm_linearize(cg_plan plan, const double *z0, double *zT, int64_t n_steps, void *workspace,
                                   void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_tlm_linearize");
     return tlm_linearized(plan, z0, zT, nullptr, nullptr, 0, n_steps, false, workspace, stream);
 }
 
 CG_API cg_status cg_tlm_apply(cg_plan plan, const double *dz0, double *dzT, int32_t n_tangents, int64_t n_steps,
                               void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_tlm_apply");
     return tlm_linearized(plan, nullptr, nullptr, dz0, dzT, n_tangents, n_steps, true, workspace, stream);
 }
 
@@ -1434,6 +1443,7 @@ CG_API cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_
 CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
                                 int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_adjoint_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
     if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "cardiac_gb300.h"
 
@@ -125,5 +126,15 @@ void exp_table(double *tab, int n);
 
 // Record a message for cg_last_error() on the calling thread; returns st.
 cg_status set_last_error(cg_status st, const char *msg);
+
+// A named NVTX range for the duration of one API call, so that a timeline
+// profiler shows which library call issued which kernels (a few tens of
+// nanoseconds per call when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace cgk

@@ -282,6 +282,7 @@ CG_API cg_status cg_newton_gmres_step(cg_plan plan, const double *z0, int64_t pe
                                       int32_t max_restarts, double rtol, double *dz, double *res_hist,
                                       int32_t *n_iter, void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_newton_gmres_step");
     return gmres_step(plan, z0, period_steps, restart, max_restarts, rtol, dz, res_hist, n_iter, workspace, stream,
                       false);
 }
@@ -290,6 +291,7 @@ CG_API cg_status cg_newton_gmres_step_linearized(cg_plan plan, const double *z0,
                                                  int32_t restart, int32_t max_restarts, double rtol, double *dz,
                                                  double *res_hist, int32_t *n_iter, void *workspace, void *stream)
 {
+    cgk::NvtxRange nvtx_range("cg_newton_gmres_step_linearized");
     return gmres_step(plan, z0, period_steps, restart, max_restarts, rtol, dz, res_hist, n_iter, workspace, stream,
                       true);
 }
