@@ -134,10 +134,12 @@ typedef struct cg_tuning {
     int32_t schedule;      /* 0: static (equal cells per block, equal strip-rows per warp,
                               computed at plan creation); 1: atomic tile queue per stage
                               (tiles of 32*cells_x columns by `rows` rows, largest
-                              instances first); 2: temporal blocking of cg_run for small
-                              grids: each block advances a tile and its halo through `rows`
-                              steps (default 2) in shared memory per grid barrier, with
-                              `threads` per block (default 256); one instance, MIRROR or
+                              instances first); 2: temporal blocking of cg_run and
+                              cg_batch_run for small grids: the instances are cut into
+                              tiles (one per block for a single instance; the blocks loop
+                              over the tiles of a batch), each advanced with its halo
+                              through `rows` steps (default 2) in shared memory per grid
+                              barrier, with `threads` per block (default 256); MIRROR or
                               CLAMP ghosts, EULER/HEUN/RK4 only (else CG_EUNSUPPORTED), the
                               same results bit for bit; the plan's other entry points use
                               the default launch shape */

@@ -145,7 +145,7 @@ struct cg_plan_s {
     const void *kernel = nullptr;
     // temporal blocking of cg_run (tuning.schedule = 2): steps per pass (0 =
     // off), tile size, tiles along x, blocks, threads, window cells, kernel
-    int32_t tb_k = 0, tb_tx = 0, tb_ty = 0, tb_tiles_x = 0, tb_blocks = 0, tb_threads = 0, tb_wmax = 0;
+    int32_t tb_k = 0, tb_tx = 0, tb_ty = 0, tb_tiles = 0, tb_blocks = 0, tb_threads = 0, tb_wmax = 0;
     size_t tb_smem = 0;
     const void *tb_kernel = nullptr;
     int nblocks = 0;
@@ -480,56 +480,123 @@ void halo_dependencies(const std::vector<int32_t> &nxs, const std::vector<int32_
 // unless the grid is thinner than that, every tile resident at once (the
 // launch is cooperative), the window (tile plus k n_s halo cells, clipped
 // at the ghost layer) in shared memory.
-cg_status tb_setup(cg_plan_s *P, const cg_problem &p)
+// Tiles of the temporally blocked kernel: one uniform tile size for all
+// instances (clipped at their edges), windows (tile + halo) that fit shared
+// memory.  One instance: one tile per block, the tiles grown until they are
+// all resident together.  A batch: the largest square tile whose window
+// fits, blocks looping over the tiles.
+cg_status tb_setup(cg_plan_s *P)
 {
     P->tb_kernel = lookup_tb_kernel(P->kmodel, P->stencil, P->scheme);
     if (!P->tb_kernel) return fail(CG_EUNSUPPORTED, "no temporally blocked kernel for this problem");
-    const int nx = (int)p.nx, ny = (int)p.ny, H = P->tb_k * P->ns;
+    const int H = P->tb_k * P->ns;
     int dev_smem = 0;
     cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (e != cudaSuccess) return cuda_fail(e, "device attribute");
-    const int64_t cells = (int64_t)nx * ny;
-    const int64_t per = (cells + P->num_sms - 1) / P->num_sms;
-    int ty = (int)std::ceil(std::sqrt((double)per)), tx = ty;
-    if (ty > ny) {
-        ty = ny;
-        tx = (int)((per + ny - 1) / ny);
+    const bool single = P->inst.size() == 1;
+    int maxnx = 1, maxny = 1;
+    int64_t cells = 0;
+    for (const Inst &I : P->inst) {
+        maxnx = std::max(maxnx, I.nx);
+        maxny = std::max(maxny, I.ny);
+        cells += (int64_t)I.nx * I.ny;
     }
-    tx = std::max(1, std::min(tx, nx));
-    for (int attempt = 0; attempt < 4096; ++attempt) {
-        const int tiles_x = (nx + tx - 1) / tx, tiles_y = (ny + ty - 1) / ty;
-        int wmax = 0;
-        for (int by = 0; by < tiles_y; ++by)
+    // largest window of tiles tx x ty over all instances, and the tile count
+    auto windows = [&](int tx, int ty, int &wmax, int64_t &ntiles) {
+        wmax = 0;
+        ntiles = 0;
+        for (const Inst &I : P->inst) {
+            const int tiles_x = (I.nx + tx - 1) / tx, tiles_y = (I.ny + ty - 1) / ty;
+            ntiles += (int64_t)tiles_x * tiles_y;
+            // a window's width and height depend on its column and row alone
+            int wx = 0, wy = 0;
             for (int bx = 0; bx < tiles_x; ++bx) {
-                int w0, w1, h0, h1;
-                cgk::tb_window(bx * tx, std::min(bx * tx + tx, nx), nx, H, w0, w1);
-                cgk::tb_window(by * ty, std::min(by * ty + ty, ny), ny, H, h0, h1);
-                wmax = std::max(wmax, (w1 - w0) * (h1 - h0));
+                int w0, w1;
+                cgk::tb_window(bx * tx, std::min(bx * tx + tx, I.nx), I.nx, H, w0, w1);
+                wx = std::max(wx, w1 - w0);
             }
-        const size_t smem = cgk::tb_smem_bytes(P->nv, P->ns, wmax);
-        if (smem + sizeof(Inst) > (size_t)dev_smem)
-            return fail(CG_EUNSUPPORTED, "temporal blocking: a tile and its halo (%d steps) need %zu bytes of "
-                                         "shared memory, the device has %d", P->tb_k, smem, dev_smem);
-        e = cudaFuncSetAttribute(P->tb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "shared memory attribute");
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, P->tb_kernel, P->tb_threads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-        if (occ >= 1 && tiles_x * tiles_y <= occ * P->num_sms) {
-            P->tb_tx = tx;
-            P->tb_ty = ty;
-            P->tb_tiles_x = tiles_x;
-            P->tb_blocks = tiles_x * tiles_y;
-            P->tb_wmax = wmax;
-            P->tb_smem = smem;
-            return CG_OK;
+            for (int by = 0; by < tiles_y; ++by) {
+                int h0, h1;
+                cgk::tb_window(by * ty, std::min(by * ty + ty, I.ny), I.ny, H, h0, h1);
+                wy = std::max(wy, h1 - h0);
+            }
+            wmax = std::max(wmax, wx * wy);
         }
-        // too many tiles to be resident together: make them larger
-        if (tx < nx && (tx <= ty || ty >= ny)) ++tx;
-        else if (ty < ny) ++ty;
-        else break;
+    };
+    auto finish = [&](int tx, int ty, int wmax, int64_t ntiles, int blocks, size_t smem) {
+        P->tb_tx = tx;
+        P->tb_ty = ty;
+        P->tb_wmax = wmax;
+        P->tb_smem = smem;
+        P->tb_tiles = (int32_t)ntiles;
+        P->tb_blocks = blocks;
+        int32_t begin = 0;
+        for (Inst &I : P->inst) {
+            I.tb_tiles_x = (I.nx + tx - 1) / tx;
+            I.tb_tile_begin = begin;
+            begin += I.tb_tiles_x * ((I.ny + ty - 1) / ty);
+        }
+        return CG_OK;
+    };
+    auto occupancy = [&](size_t smem, int &occ) -> cg_status {
+        cudaError_t err = cudaFuncSetAttribute(P->tb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return cuda_fail(err, "shared memory attribute");
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, P->tb_kernel, P->tb_threads, smem);
+        if (err != cudaSuccess) return cuda_fail(err, "occupancy query");
+        return CG_OK;
+    };
+    const size_t inst_smem = sizeof(Inst) + 16;
+    const int64_t per = (cells + P->num_sms - 1) / P->num_sms;
+    if (single) {
+        const int nx = P->inst[0].nx, ny = P->inst[0].ny;
+        int ty = (int)std::ceil(std::sqrt((double)per)), tx = ty;
+        if (ty > ny) {
+            ty = ny;
+            tx = (int)((per + ny - 1) / ny);
+        }
+        tx = std::max(1, std::min(tx, nx));
+        for (int attempt = 0; attempt < 4096; ++attempt) {
+            int wmax = 0;
+            int64_t ntiles = 0;
+            windows(tx, ty, wmax, ntiles);
+            const size_t smem = cgk::tb_smem_bytes(P->nv, P->ns, wmax);
+            if (smem + inst_smem > (size_t)dev_smem)
+                return fail(CG_EUNSUPPORTED, "temporal blocking: a tile and its halo (%d steps) need %zu bytes of "
+                                             "shared memory, the device has %d", P->tb_k, smem, dev_smem);
+            int occ = 0;
+            const cg_status st = occupancy(smem, occ);
+            if (st != CG_OK) return st;
+            if (occ >= 1 && ntiles <= (int64_t)occ * P->num_sms)
+                return finish(tx, ty, wmax, ntiles, (int)ntiles, smem);
+            // too many tiles to be resident together: make them larger
+            if (tx < nx && (tx <= ty || ty >= ny)) ++tx;
+            else if (ty < ny) ++ty;
+            else break;
+        }
+        return fail(CG_EUNSUPPORTED, "temporal blocking: no tile size fits this device");
     }
-    return fail(CG_EUNSUPPORTED, "temporal blocking: no tile size fits this device");
+    int side = (int)std::ceil(std::sqrt((double)per));
+    side = std::max(1, std::min(side, std::max(maxnx, maxny)));
+    for (;;) {
+        const int tx = std::min(side, maxnx), ty = std::min(side, maxny);
+        int wmax = 0;
+        int64_t ntiles = 0;
+        windows(tx, ty, wmax, ntiles);
+        const size_t smem = cgk::tb_smem_bytes(P->nv, P->ns, wmax);
+        if (smem + inst_smem <= (size_t)dev_smem && ntiles < (int64_t)1 << 30) {
+            int occ = 0;
+            const cg_status st = occupancy(smem, occ);
+            if (st != CG_OK) return st;
+            if (occ >= 1) {
+                const int64_t resident = (int64_t)occ * P->num_sms;
+                return finish(tx, ty, wmax, ntiles, (int)std::min<int64_t>(ntiles, resident), smem);
+            }
+        }
+        if (side == 1)
+            return fail(CG_EUNSUPPORTED, "temporal blocking: a 1 x 1 tile and its halo (%d steps) do not fit "
+                                         "shared memory", P->tb_k);
+        side = std::max(1, side * 7 / 8);
+    }
 }
 
 cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tune, cg_plan *out)
@@ -575,10 +642,10 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         // default launch shape
         P->tb_k = tune->rows ? tune->rows : 2;
         P->tb_threads = tune->threads ? tune->threads : 256;
-        if (n_inst != 1 || p0.bc == CG_BC_PERIODIC || gate_scheme(p0.scheme)) {
+        if (p0.bc == CG_BC_PERIODIC || gate_scheme(p0.scheme)) {
             delete P;
-            return fail(CG_EUNSUPPORTED, "temporal blocking needs one instance, mirror or clamp ghosts and an "
-                                         "explicit Euler, Heun or RK4 scheme");
+            return fail(CG_EUNSUPPORTED, "temporal blocking needs mirror or clamp ghosts and an explicit Euler, "
+                                         "Heun or RK4 scheme");
         }
         if (P->tb_k < 1 || P->tb_k > 64 || P->tb_threads < 64 || P->tb_threads > 512 || (P->tb_threads % 32)) {
             delete P;
@@ -684,7 +751,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
                         (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
     }
     if (e == cudaSuccess && P->tb_k > 0) {
-        const cg_status st = tb_setup(P, probs[0]);
+        const cg_status st = tb_setup(P);
         if (st != CG_OK) {
             delete P;
             return st;
@@ -958,19 +1025,17 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
     const int64_t G = n_steps * plan->ns;
     void *args[] = {&a};
 
-    if (plan->tb_k > 0 && !tab) {
+    if (plan->tb_k > 0) {
         // temporally blocked: one cooperative launch, one grid barrier per
         // tb_k steps (cg_tblock.cuh)
         cgk::TbArgs t;
         std::memset(&t, 0, sizeof t);
         t.tx = plan->tb_tx;
         t.ty = plan->tb_ty;
-        t.tiles_x = plan->tb_tiles_x;
+        t.n_tiles = plan->tb_tiles;
         t.k = plan->tb_k;
         t.wmax = plan->tb_wmax;
-        t.alias = any_alias ? 1 : 0;
         t.n_steps = n_steps;
-        t.zscr = a.ws + plan->inst[0].ws_off;
         a.persistent = 1;
         a.nblocks_expect = (uint32_t)plan->tb_blocks;
         a.stuck_barrier = (plan->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
@@ -992,9 +1057,14 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
         if (e != cudaSuccess) return cuda_fail(e, "temporally blocked kernel launch");
         const int64_t passes = (n_steps + plan->tb_k - 1) / plan->tb_k;
         if (any_alias && ((passes - 1) & 1) == 0) {
-            // in place with an odd number of passes: the result is in the scratch copy
-            e = cudaMemcpyAsync(pout[0], t.zscr, inst_bytes(0), cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
+            // in place with an odd number of passes: the result of each
+            // in-place instance is in its scratch copy
+            for (size_t k = 0; k < n_inst; ++k) {
+                if (pin[k] != pout[k]) continue;
+                e = cudaMemcpyAsync(pout[k], a.ws + plan->inst[k].ws_off, inst_bytes(k), cudaMemcpyDeviceToDevice,
+                                    s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final)");
+            }
         }
         return CG_OK;
     }

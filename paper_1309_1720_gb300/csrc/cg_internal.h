@@ -22,6 +22,8 @@ struct Inst {
     int32_t tiles_x, tiles_y;
     int32_t tile_begin;      // global tile id of this instance's first tile
     int32_t vec_ok;          // nx even and packed offset even: rows start 16-byte aligned
+    int32_t tb_tiles_x;      // temporal blocking: tiles along x of this instance
+    int32_t tb_tile_begin;   // temporal blocking: global index of its first tile
     int64_t off;             // element offset of the instance in packed state buffers
     int64_t ws_off;          // element offset of the instance's scratch block in the workspace
     double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights

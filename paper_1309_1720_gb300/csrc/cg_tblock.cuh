@@ -1,12 +1,13 @@
-// Temporally blocked stepping for small grids (one instance, mirror or clamp
-// ghosts).
+// Temporally blocked stepping for small grids (one instance or a batch,
+// mirror or clamp ghosts).
 //
 // On a small grid every stage of the persistent stage kernel costs about one
 // grid barrier plus one L2 round trip, far more than its arithmetic.  Here
-// each block owns a rectangular tile, loads it with a halo of H = K n_s cells
-// (K steps of n_s stages), advances the tile through all H stages in shared
-// memory, the region it updates shrinking by one cell per stage (a stage
-// reads one ring of neighbours), and writes the tile back: one grid barrier
+// the instances are cut into rectangular tiles (a single instance: one per
+// block; a batch: the blocks loop over them).  A tile is loaded with a halo
+// of H = K n_s cells (K steps of n_s stages), advanced through all H stages
+// in shared memory, the region it updates shrinking by one cell per stage (a
+// stage reads one ring of neighbours), and written back: one grid barrier
 // per K steps instead of one per stage, at the price of recomputing the halo.
 // Ghost points (Fig. 1) at the domain's edges are refilled from the cells
 // they mirror after every stage, so the shrinking region never needs values
@@ -26,20 +27,20 @@ namespace cgk {
 
 struct TbArgs {
     int32_t tx, ty;          // tile size (cells)
-    int32_t tiles_x;         // tiles along x (block b owns tile (b % tiles_x, b / tiles_x))
+    int32_t n_tiles;         // tiles of all instances (instance i owns [tb_tile_begin, + tb_tiles))
     int32_t k;               // steps per pass
     int32_t wmax;            // shared window capacity in cells (per array)
-    int32_t alias;           // z_in == z_out
     int64_t n_steps;
-    double *zscr;            // scratch state for the ping-pong between passes
 };
 
-// Output buffer of pass p of P (see cg_run): the last pass writes z_out,
-// except in place where the first pass must not overwrite its input.
-__device__ __forceinline__ double *tb_dst(const RunArgs &a, const TbArgs &t, int64_t p, int64_t P)
+// Output buffer of an instance in pass p of P: the last pass writes its
+// output, except in place (input == output) where the first pass must not
+// overwrite its input; the other passes alternate with the instance's
+// scratch copy.
+__device__ __forceinline__ double *tb_dst(double *out, double *scr, bool alias, int64_t p, int64_t P)
 {
-    if (t.alias) return (p & 1) ? a.z_out : t.zscr;
-    return (((P - 1 - p) & 1) == 0) ? a.z_out : t.zscr;
+    if (alias) return (p & 1) ? out : scr;
+    return (((P - 1 - p) & 1) == 0) ? out : scr;
 }
 
 // Window [w0, w1) along one axis for the tile [t0, t1) of an axis of n
@@ -59,20 +60,10 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     constexpr int NV = MD::NV, ND = MD::ND;
     extern __shared__ double sm[];
     __shared__ Inst s_inst;
-    if (threadIdx.x == 0) s_inst = a.inst[0];
-    __syncthreads();
-    const Inst &I = s_inst;
-    const int nx = I.nx, ny = I.ny, bc = a.bc;
+    int cur = -1;                            // instance held in s_inst (the same in every thread)
+    const int bc = a.bc;
     const bool mirror = (bc == CG_BC_MIRROR);
-    const int x0 = (blockIdx.x % t.tiles_x) * t.tx, y0 = (blockIdx.x / t.tiles_x) * t.ty;
-    const int x1 = min(x0 + t.tx, nx), y1 = min(y0 + t.ty, ny);    // tile [x0, x1) x [y0, y1)
     const int Hmax = t.k * NS;
-    // window: the tile with Hmax cells of halo; where that reaches the
-    // domain's edge it ends at the ghost layer instead (tb_window)
-    int gx0, gx1, gy0, gy1;
-    tb_window(x0, x1, nx, Hmax, gx0, gx1);
-    tb_window(y0, y1, ny, Hmax, gy0, gy1);
-    const int WX = gx1 - gx0;
     const int WS = t.wmax;
     // arrays (each NV planes of WS): NS == 1: YA, YB; else Z, ACC, YA, YB
     double *Z = sm;
@@ -80,195 +71,284 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     double *YA = ACC + (NS > 1 ? NV * WS : 0);
     double *YB = YA + NV * WS;
     if (NS == 1) Z = YA;
-    auto at = [&](int gx, int gy) { return (gy - gy0) * WX + (gx - gx0); };
-    // checked build: (gx, gy) is a window cell and the window fits the arrays
-    const bool win_fits = WX * (gy1 - gy0) <= WS;
-    auto in_window = [&](int gx, int gy) {
-        return win_fits && gx >= gx0 && gx < gx1 && gy >= gy0 && gy < gy1;
-    };
-
-    double wx[ND > 0 ? ND : 1], wy[ND > 0 ? ND : 1], wd[ND > 0 ? ND : 1], wt[ND > 0 ? ND : 1];
-#pragma unroll
-    for (int f = 0; f < ND; ++f) {
-        wx[f] = I.wx[f];
-        wy[f] = I.wy[f];
-        wd[f] = I.wd[f];
-        wt[f] = I.wt[f];
-    }
-    const typename MD::Coef coef = MD::coef(I);
     const double *mp = a.mp;
-    const int64_t plane = (int64_t)nx * ny;
-
     uint32_t bad = 0;
-    // Ghost points of buffer B on the region [xl, xh) x [yl, yh): x ghosts of
-    // its rows first, then whole y-ghost rows (corners follow both flips).
-    auto fill_ghosts = [&](double *B, int xl, int xh, int yl, int yh) {
-        const int gx_lo = mirror ? 1 : 0, gx_hi = mirror ? nx - 2 : nx - 1;
-        const int gy_lo = mirror ? 1 : 0, gy_hi = mirror ? ny - 2 : ny - 1;
-        const bool left = (xl == 0), right = (xh == nx), bot = (yl == 0), top = (yh == ny);
-        if (!(left || right || bot || top)) return;        // block-uniform: interior tiles skip both syncs
-        const int nrow = yh - yl;
-        for (int q = threadIdx.x; q < 2 * nrow; q += blockDim.x) {
-            const int y = yl + (q >> 1);
-            const bool lft = (q & 1) == 0;
-            if (lft ? !left : !right) continue;
-            if constexpr (BOUNDS_CHECK) {
-                if (!in_window(lft ? -1 : nx, y) || !in_window(lft ? gx_lo : gx_hi, y)) {
-                    bad |= CG_DEV_BOUNDS;
-                    continue;
-                }
+
+    // Per-tile constants (one tile of one instance).
+    struct TbCtx {
+        int i, nx, ny, x0, y0, x1, y1, gx0, gx1, gy0, gy1, WX;
+        double wx[ND > 0 ? ND : 1], wy[ND > 0 ? ND : 1], wd[ND > 0 ? ND : 1], wt[ND > 0 ? ND : 1];
+        typename MD::Coef coef;
+        const double *zin;
+        double *zout, *scr;
+    };
+    // The tile's instance (every thread finds the same one; a single
+    // instance needs no search) is staged in shared memory when it changes.
+    auto make_ctx = [&](int tile) {
+        int i = 0;
+        if (a.n_inst > 1) {
+            int hi = a.n_inst - 1;
+            while (i < hi) {
+                const int mid = (i + hi + 1) >> 1;
+                if (a.inst[mid].tb_tile_begin <= tile) i = mid; else hi = mid - 1;
             }
-            const int dst = at(lft ? -1 : nx, y), src = at(lft ? gx_lo : gx_hi, y);
-#pragma unroll
-            for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
         }
-        __syncthreads();
-        const int cl = left ? xl - 1 : xl, ch = right ? xh + 1 : xh;
-        const int ncol = ch - cl;
-        for (int q = threadIdx.x; q < 2 * ncol; q += blockDim.x) {
-            const int x = cl + (q >> 1);
-            const bool lo = (q & 1) == 0;
-            if (lo ? !bot : !top) continue;
-            if constexpr (BOUNDS_CHECK) {
-                if (!in_window(x, lo ? -1 : ny) || !in_window(x, lo ? gy_lo : gy_hi)) {
-                    bad |= CG_DEV_BOUNDS;
-                    continue;
-                }
-            }
-            const int dst = at(x, lo ? -1 : ny), src = at(x, lo ? gy_lo : gy_hi);
-#pragma unroll
-            for (int f = 0; f < NV; ++f) B[f * WS + dst] = B[f * WS + src];
+        if (i != cur) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_inst = a.inst[i];
+            __syncthreads();
+            cur = i;
         }
-        __syncthreads();
+        const Inst &I = s_inst;
+        TbCtx c;
+        c.i = i;
+        c.nx = I.nx;
+        c.ny = I.ny;
+        const int lt = tile - I.tb_tile_begin;
+        c.x0 = (lt % I.tb_tiles_x) * t.tx;
+        c.y0 = (lt / I.tb_tiles_x) * t.ty;
+        c.x1 = min(c.x0 + t.tx, c.nx);
+        c.y1 = min(c.y0 + t.ty, c.ny);
+        // window: the tile with Hmax cells of halo; where that reaches the
+        // domain's edge it ends at the ghost layer instead (tb_window)
+        tb_window(c.x0, c.x1, c.nx, Hmax, c.gx0, c.gx1);
+        tb_window(c.y0, c.y1, c.ny, Hmax, c.gy0, c.gy1);
+        c.WX = c.gx1 - c.gx0;
+#pragma unroll
+        for (int f = 0; f < ND; ++f) {
+            c.wx[f] = I.wx[f];
+            c.wy[f] = I.wy[f];
+            c.wd[f] = I.wd[f];
+            c.wt[f] = I.wt[f];
+        }
+        c.coef = MD::coef(I);
+        c.zin = a.zin_tab ? a.zin_tab[i] : a.z_in + I.off;
+        c.zout = a.zout_tab ? a.zout_tab[i] : a.z_out + I.off;
+        c.scr = a.ws + I.ws_off;
+        return c;
     };
 
     const int64_t P = (t.n_steps + t.k - 1) / t.k;
-    const bool tb_ok = !BOUNDS_CHECK || (win_fits && WX >= 3 && gy1 - gy0 >= 3);
-    if (!tb_ok) bad |= CG_DEV_BOUNDS;
-    for (int64_t p = 0; p < P; ++p) {
-        const int64_t rest = t.n_steps - p * t.k;
-        const int kp = (int)(rest < t.k ? rest : t.k);
-        const int H = kp * NS;
-        const double *src = (p == 0) ? a.z_in : tb_dst(a, t, p - 1, P);
-        double *dst = tb_dst(a, t, p, P);
+    // Pass p (H stages) of one tile: load the window, advance it, write the
+    // tile back.
+    auto run_tile = [&](const TbCtx &c, int64_t p, int H) {
+        const int nx = c.nx, ny = c.ny;
+        const int x0 = c.x0, y0 = c.y0, x1 = c.x1, y1 = c.y1;
+        const int gx0 = c.gx0, gx1 = c.gx1, gy0 = c.gy0, gy1 = c.gy1, WX = c.WX;
+        auto at = [&](int gx, int gy) { return (gy - gy0) * WX + (gx - gx0); };
+        // checked build: (gx, gy) is a window cell and the window fits the arrays
+        const bool win_fits = WX * (gy1 - gy0) <= WS;
+        auto in_window = [&](int gx, int gy) {
+            return win_fits && gx >= gx0 && gx < gx1 && gy >= gy0 && gy < gy1;
+        };
+        double wx[ND > 0 ? ND : 1], wy[ND > 0 ? ND : 1], wd[ND > 0 ? ND : 1], wt[ND > 0 ? ND : 1];
+#pragma unroll
+        for (int f = 0; f < ND; ++f) {
+            wx[f] = c.wx[f];
+            wy[f] = c.wy[f];
+            wd[f] = c.wd[f];
+            wt[f] = c.wt[f];
+        }
+        const typename MD::Coef coef = c.coef;
+        const int64_t plane = (int64_t)nx * ny;
+        const bool alias = (c.zin == c.zout);
+        const double *src = (p == 0) ? c.zin : tb_dst(c.zout, c.scr, alias, p - 1, P);
+        double *dst = tb_dst(c.zout, c.scr, alias, p, P);
+
+        // Ghost points of buffer B on the region [xl, xh) x [yl, yh): x
+        // ghosts of its rows first, then whole y-ghost rows (corners
+        // follow both flips).
+        auto fill_ghosts = [&](double *B, int xl, int xh, int yl, int yh) {
+            const int gx_lo = mirror ? 1 : 0, gx_hi = mirror ? nx - 2 : nx - 1;
+            const int gy_lo = mirror ? 1 : 0, gy_hi = mirror ? ny - 2 : ny - 1;
+            const bool left = (xl == 0), right = (xh == nx), bot = (yl == 0), top = (yh == ny);
+            if (!(left || right || bot || top)) return;    // block-uniform: interior tiles skip both syncs
+            const int nrow = yh - yl;
+            for (int q = threadIdx.x; q < 2 * nrow; q += blockDim.x) {
+                const int y = yl + (q >> 1);
+                const bool lft = (q & 1) == 0;
+                if (lft ? !left : !right) continue;
+                if constexpr (BOUNDS_CHECK) {
+                    if (!in_window(lft ? -1 : nx, y) || !in_window(lft ? gx_lo : gx_hi, y)) {
+                        bad |= CG_DEV_BOUNDS;
+                        continue;
+                    }
+                }
+                const int d = at(lft ? -1 : nx, y), sidx = at(lft ? gx_lo : gx_hi, y);
+#pragma unroll
+                for (int f = 0; f < NV; ++f) B[f * WS + d] = B[f * WS + sidx];
+            }
+            __syncthreads();
+            const int cl = left ? xl - 1 : xl, ch = right ? xh + 1 : xh;
+            const int ncol = ch - cl;
+            for (int q = threadIdx.x; q < 2 * ncol; q += blockDim.x) {
+                const int x = cl + (q >> 1);
+                const bool lo = (q & 1) == 0;
+                if (lo ? !bot : !top) continue;
+                if constexpr (BOUNDS_CHECK) {
+                    if (!in_window(x, lo ? -1 : ny) || !in_window(x, lo ? gy_lo : gy_hi)) {
+                        bad |= CG_DEV_BOUNDS;
+                        continue;
+                    }
+                }
+                const int d = at(x, lo ? -1 : ny), sidx = at(x, lo ? gy_lo : gy_hi);
+#pragma unroll
+                for (int f = 0; f < NV; ++f) B[f * WS + d] = B[f * WS + sidx];
+            }
+            __syncthreads();
+        };
+
         // checked build: a window that does not fit its arrays skips every
-        // access of this block (it still joins the grid barriers)
-        if (tb_ok) {
-            // load the window's domain cells: the tile plus H cells of halo
-            {
-                const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
-                const int w = xh - xl, n = w * (yh - yl);
-                for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                    const int gx = xl + c % w, gy = yl + c / w;
-                    if constexpr (BOUNDS_CHECK) {
-                        if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(src)) {
-                            bad |= CG_DEV_BOUNDS;
-                            continue;
-                        }
-                    }
-#pragma unroll
-                    for (int f = 0; f < NV; ++f)
-                        Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
-                }
-                __syncthreads();
-                fill_ghosts(Z, xl, xh, yl, yh);
-            }
-            double *Yin = Z;
-            for (int g = 1; g <= H; ++g) {
-                const int s = (g - 1) % NS;
-                const bool last = (s == NS - 1);
-                const int rad = H - g;
-                const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
-                const int w = xh - xl, n = w * (yh - yl);
-                double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
-                const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
-                // every thread runs the same number of iterations, so the model's
-                // warp-uniform paths see whole warps; surplus threads repeat the
-                // last cell and store nothing
-                for (int base = 0; base < n; base += blockDim.x) {
-                    const int c = base + (int)threadIdx.x;
-                    const bool act = c < n;
-                    const int cc = act ? c : n - 1;
-                    const int gx = xl + cc % w, gy = yl + cc / w;
-                    int li = at(gx, gy);
-                    bool act_ok = act;
-                    if constexpr (BOUNDS_CHECK) {
-                        // the cell and its eight neighbours inside the window; a
-                        // failed check computes a harmless interior cell instead
-                        // and stores nothing (the model still sees whole warps)
-                        if (!(in_window(gx - 1, gy - 1) && in_window(gx + 1, gy + 1)) && n > 0) {
-                            bad |= CG_DEV_BOUNDS;
-                            li = WX + 1;
-                            act_ok = false;
-                        }
-                    }
-                    double zc[NV];
-#pragma unroll
-                    for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
-                    double F[NV];
-                    MD::local(coef, mp, zc, F);
-#pragma unroll
-                    for (int f = 0; f < ND; ++f) {
-                        const double *Q = Yin + f * WS;
-                        const double Wv = Q[li - 1], Ev = Q[li + 1];
-                        if (ST == CG_STENCIL9) {
-                            const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
-                            const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
-                            const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
-                            const double acc_f = fma(wd[f], Tl + Th, F[f]);
-                            F[f] = fma(wx[f], Wv + Ev, acc_f);
-                        } else {
-                            double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
-                            F[f] = fma(wx[f], Wv + Ev, acc_f);
-                        }
-                    }
-                    if (act_ok) {
-#pragma unroll
-                        for (int f = 0; f < NV; ++f) {
-                            const int o = f * WS + li;
-                            if (NS == 1) {
-                                Yout[o] = fma(ca, F[f], zc[f]);
-                            } else if (s == 0) {
-                                ACC[o] = fma(ca, F[f], zc[f]);
-                                Yout[o] = fma(cyv, F[f], zc[f]);
-                            } else if (!last) {
-                                ACC[o] = fma(ca, F[f], ACC[o]);
-                                Yout[o] = fma(cyv, F[f], Z[o]);
-                            } else {
-                                Yout[o] = fma(ca, F[f], ACC[o]);
-                            }
-                        }
+        // access of this tile (the block still joins the grid barriers)
+        const bool tb_ok = !BOUNDS_CHECK || (win_fits && WX >= 3 && gy1 - gy0 >= 3);
+        if (!tb_ok) {
+            bad |= CG_DEV_BOUNDS;
+            return;
+        }
+        // load the window's domain cells: the tile plus H cells of halo
+        {
+            const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
+            const int w = xh - xl, n = w * (yh - yl);
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int gx = xl + c % w, gy = yl + c / w;
+                if constexpr (BOUNDS_CHECK) {
+                    if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(src)) {
+                        bad |= CG_DEV_BOUNDS;
+                        continue;
                     }
                 }
-                __syncthreads();
-                fill_ghosts(Yout, xl, xh, yl, yh);
-                Yin = Yout;
+#pragma unroll
+                for (int f = 0; f < NV; ++f)
+                    Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
             }
-            // write the tile back
-            {
-                const int w = x1 - x0, n = w * (y1 - y0);
-                for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                    const int gx = x0 + c % w, gy = y0 + c / w;
-                    if constexpr (BOUNDS_CHECK) {
-                        if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(dst)) {
-                            bad |= CG_DEV_BOUNDS;
-                            continue;
-                        }
+            __syncthreads();
+            fill_ghosts(Z, xl, xh, yl, yh);
+        }
+        double *Yin = Z;
+        for (int g = 1; g <= H; ++g) {
+            const int s = (g - 1) % NS;
+            const bool last = (s == NS - 1);
+            const int rad = H - g;
+            const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
+            const int w = xh - xl, n = w * (yh - yl);
+            double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
+            const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
+            // every thread runs the same number of iterations, so the
+            // model's warp-uniform paths see whole warps; surplus threads
+            // repeat the last cell and store nothing
+            for (int base = 0; base < n; base += blockDim.x) {
+                const int c = base + (int)threadIdx.x;
+                const bool act = c < n;
+                const int cc = act ? c : n - 1;
+                const int gx = xl + cc % w, gy = yl + cc / w;
+                int li = at(gx, gy);
+                bool act_ok = act;
+                if constexpr (BOUNDS_CHECK) {
+                    // the cell and its eight neighbours inside the window;
+                    // a failed check computes a harmless interior cell
+                    // instead and stores nothing (whole warps stay)
+                    if (!(in_window(gx - 1, gy - 1) && in_window(gx + 1, gy + 1))) {
+                        bad |= CG_DEV_BOUNDS;
+                        li = WX + 1;
+                        act_ok = false;
                     }
+                }
+                double zc[NV];
+#pragma unroll
+                for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
+                double F[NV];
+                MD::local(coef, mp, zc, F);
+#pragma unroll
+                for (int f = 0; f < ND; ++f) {
+                    const double *Q = Yin + f * WS;
+                    const double Wv = Q[li - 1], Ev = Q[li + 1];
+                    if (ST == CG_STENCIL9) {
+                        const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
+                        const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
+                        const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
+                        const double acc_f = fma(wd[f], Tl + Th, F[f]);
+                        F[f] = fma(wx[f], Wv + Ev, acc_f);
+                    } else {
+                        double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
+                        F[f] = fma(wx[f], Wv + Ev, acc_f);
+                    }
+                }
+                if (act_ok) {
 #pragma unroll
                     for (int f = 0; f < NV; ++f) {
-                        const double v = Yin[f * WS + at(gx, gy)];
-                        bad |= nonfinite_bit(v);
-                        __stcg(dst + f * plane + (int64_t)gy * nx + gx, v);
+                        const int o = f * WS + li;
+                        if (NS == 1) {
+                            Yout[o] = fma(ca, F[f], zc[f]);
+                        } else if (s == 0) {
+                            ACC[o] = fma(ca, F[f], zc[f]);
+                            Yout[o] = fma(cyv, F[f], zc[f]);
+                        } else if (!last) {
+                            ACC[o] = fma(ca, F[f], ACC[o]);
+                            Yout[o] = fma(cyv, F[f], Z[o]);
+                        } else {
+                            Yout[o] = fma(ca, F[f], ACC[o]);
+                        }
                     }
+                }
+            }
+            __syncthreads();
+            fill_ghosts(Yout, xl, xh, yl, yh);
+            Yin = Yout;
+        }
+        // write the tile back
+        {
+            const int w = x1 - x0, n = w * (y1 - y0);
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int gx = x0 + c % w, gy = y0 + c / w;
+                if constexpr (BOUNDS_CHECK) {
+                    if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(dst)) {
+                        bad |= CG_DEV_BOUNDS;
+                        continue;
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NV; ++f) {
+                    const double v = Yin[f * WS + at(gx, gy)];
+                    bad |= nonfinite_bit(v);
+                    __stcg(dst + f * plane + (int64_t)gy * nx + gx, v);
                 }
             }
         }
+    };
+
+    auto pass_end = [&](int64_t p) {
         if (p + 1 < P) {
             const unsigned long long target = (unsigned long long)(p + 1) * a.nblocks_expect +
                                               ((p == 0 && a.stuck_barrier) ? 1u : 0u);
-            if (!grid_barrier(reinterpret_cast<unsigned long long *>(a.sync), a.status, a.timeout_ns, target))
-                return;
+            return grid_barrier(reinterpret_cast<unsigned long long *>(a.sync), a.status, a.timeout_ns, target);
+        }
+        return true;
+    };
+    auto pass_depth = [&](int64_t p) {
+        const int64_t rest = t.n_steps - p * t.k;
+        return (int)(rest < t.k ? rest : t.k) * NS;
+    };
+    if (t.n_tiles <= (int)gridDim.x) {
+        // at most one tile per block (a single instance): its constants once
+        TbCtx c;
+        const bool has = (int)blockIdx.x < t.n_tiles;
+        if (has) c = make_ctx(blockIdx.x);
+        for (int64_t p = 0; p < P; ++p) {
+            if (has) run_tile(c, p, pass_depth(p));
+            if (!pass_end(p)) return;
+        }
+    } else {
+        // a batch: the blocks take tiles blockIdx.x, + gridDim.x, ... of all
+        // instances in every pass
+        for (int64_t p = 0; p < P; ++p) {
+            const int H = pass_depth(p);
+            for (int tile = blockIdx.x; tile < t.n_tiles; tile += gridDim.x) {
+                const TbCtx c = make_ctx(tile);
+                run_tile(c, p, H);
+                // the next tile reuses the arrays (block-uniform)
+                if (tile + (int)gridDim.x < t.n_tiles) __syncthreads();
+            }
+            if (!pass_end(p)) return;
         }
     }
     bad = __reduce_or_sync(CG_FULL, bad);

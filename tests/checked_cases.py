@@ -82,6 +82,12 @@ def run_all() -> dict:
     plan.status()
     for i, r in enumerate(res):
         out["batch_%d" % i] = r.cpu().numpy()
+    for k in (1, 2):
+        tplan = Plan(probs, tuning=dict(schedule=2, rows=k))
+        res = tplan.unpack(tplan.run(tplan.pack([_state(0, p.nx, p.ny, seed=i) for i, p in enumerate(probs)]), 6))
+        tplan.status()
+        for i, r in enumerate(res):
+            out["tbatch_k%d_%d" % (k, i)] = r.cpu().numpy()
     # tangent-linear, linearized, adjoint and right-hand side
     for model in (0, 1, 2):
         for stencil in (0, 1):
