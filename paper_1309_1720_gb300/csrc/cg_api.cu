@@ -267,6 +267,8 @@ cg_status validate(const cg_problem *p, int idx)
     if (p->params)
         for (int i = 0; i < p->n_params; ++i)
             if (!finite(p->params[i])) return fail(CG_EINVAL, "problem %d: param %d not finite", idx, i);
+    if (p->model == CG_BOCF && p->params && !(p->params[28] > 0))
+        return fail(CG_EINVAL, "problem %d: the smoothed-step sharpness k must be positive", idx);
     if (p->model == CG_KARMA && p->params) {
         // tau_u, tau_v divide; Re = 0 makes 1/(1 - e^-Re) infinite
         if (p->params[0] == 0 || p->params[1] == 0 || p->params[5] == 0)
@@ -353,6 +355,48 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         P.mp[cgk::BD_ASOH] = 0.5 - prm[19] * prm[20] / 3.0;
         P.mp[cgk::BD_KSH] = prm[23] / 3.0;
         P.mp[cgk::BD_ASH] = 0.5 - prm[23] * prm[24] / 3.0;
+        // shortcut bounds of the kernel's switches t = clamp(k u + c): the
+        // largest u with fma(k, u, c) <= 0 and the smallest with >= 1
+        // (fma is correctly rounded here as on the device, and monotone in u)
+        // Bisection over the order keys of all doubles from -inf to +inf
+        // (the key map is its own inverse); k > 0 is validated.
+        auto key_of = [](double x) {
+            int64_t b;
+            std::memcpy(&b, &x, sizeof b);
+            return b ^ ((b >> 63) & INT64_C(0x7FFFFFFFFFFFFFFF));
+        };
+        auto from_key = [&](int64_t q) {
+            const int64_t b = q ^ ((q >> 63) & INT64_C(0x7FFFFFFFFFFFFFFF));
+            double x;
+            std::memcpy(&x, &b, sizeof x);
+            return x;
+        };
+        auto boundary = [&](auto pred_hi) {       // smallest key where the monotone pred_hi holds
+            int64_t lo = key_of(-INFINITY), hi = key_of(INFINITY);
+            // the key range spans almost 2^64: differences in unsigned arithmetic
+            while ((uint64_t)hi - (uint64_t)lo > 1) {
+                const int64_t mid = (int64_t)((uint64_t)lo + ((uint64_t)hi - (uint64_t)lo) / 2);
+                if (pred_hi(from_key(mid))) hi = mid; else lo = mid;
+            }
+            return hi;
+        };
+        auto last_zero = [&](double c) {
+            return from_key(boundary([&](double u) { return std::fma(k, u, c) > 0; }) - 1);
+        };
+        auto first_one = [&](double c) {
+            return from_key(boundary([&](double u) { return std::fma(k, u, c) >= 1; }));
+        };
+        auto key_bits = [&](double x) {
+            const int64_t q = key_of(x);
+            double d;
+            std::memcpy(&d, &q, sizeof d);
+            return d;
+        };
+        const double u_rest = std::min(last_zero(P.mp[cgk::BD_CV]), last_zero(P.mp[cgk::BD_CW]));
+        const double u_exc = std::max({first_one(P.mp[cgk::BD_CV]), first_one(P.mp[cgk::BD_CW]),
+                                       first_one(P.mp[cgk::BD_CVM]), first_one(P.mp[cgk::BD_CO])});
+        P.mp[cgk::BD_KREST] = key_bits(u_rest);
+        P.mp[cgk::BD_KEXC] = key_bits(u_exc);
         static_assert(cgk::BD_N <= cgk::NMP, "model constant table too small");
         I.mi[0] = I.wc[0];
     }

@@ -49,6 +49,14 @@ __device__ __forceinline__ uint32_t nonfinite_bit(double v)
     return (uint32_t)((((unsigned long long)__double_as_longlong(v)) >> 52 & 0x7ffull) == 0x7ffull);
 }
 
+// Order-preserving integer key of a double (x < y iff key(x) < key(y) for
+// non-NaN values; -0 sorts just below +0): integer-pipe comparisons.
+__device__ __forceinline__ long long order_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
 // Clamp to [0, 1] on the integer pipe: non-negative doubles order like their
 // bit patterns, and every negative double has the sign bit set.
 __device__ __forceinline__ double clamp01_int(double t)
@@ -432,6 +440,8 @@ enum {
     BD_ASH,            // 1/2 - ks us / 3
     BD_RS0,            // 1/ts1 by fast_rcp on the device (the s-gate rate where H_w = 0)
     BD_RS1,            // 1/(ts1 + (ts2 - ts1)) likewise (H_w = 1)
+    BD_KREST,          // order key (bits) of the largest u with H_v = H_w = 0 (host, exact)
+    BD_KEXC,           // order key (bits) of the smallest u with all four switches at 1
     BD_N
 };
 
@@ -508,20 +518,21 @@ template <bool TH> struct BocfModel {
     {
         const double u = z[0], v = z[1], w = z[2], s = z[3];
         const double k = mp[BP_K];
-        const double tv = clamp01_int(fma(k, u, mp[BD_CV]));
-        const double tw = clamp01_int(fma(k, u, mp[BD_CW]));
-        const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
-        const double to = clamp01_int(fma(k, u, mp[BD_CO]));
         if constexpr (!JAC) {
             // Warp-uniform shortcuts where the v and w switches are saturated
             // for every lane.  Terms multiplied by an exact 0 are dropped and
             // terms multiplied by an exact 1 kept, so the values equal the
-            // general path's.
-            const long long bv = __double_as_longlong(tv), bw = __double_as_longlong(tw);
-            const long long ONE = 0x3FF0000000000000ll;
-            if (__all_sync(CG_FULL, (bv | bw) == 0)) {
+            // general path's.  The switch t_x = clamp(k u + c_x) is 0 exactly
+            // when u is at most the largest double with fma(k, u, c_x) <= 0,
+            // and 1 from the smallest with fma(k, u, c_x) >= 1 on (fma is
+            // monotone in u); the plan holds those bounds, so the decision
+            // takes one integer compare and no switch is evaluated first.
+            const long long ku = order_key(u);
+            if (__all_sync(CG_FULL, ku <= __double_as_longlong(mp[BD_KREST]))) {
                 // resting tissue: H_v = H_w = 0 (only the u-dependent steady
                 // states and time constants near u = 0 remain)
+                const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
+                const double to = clamp01_int(fma(k, u, mp[BD_CO]));
                 const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);
                 const double Ho = (to * to) * fma(-2.0, to, 3.0);
                 const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
@@ -540,8 +551,7 @@ template <bool TH> struct BocfModel {
                 t[3] = (s_inf - s) * r_s;
                 return;
             }
-            if (__all_sync(CG_FULL, bv == ONE && bw == ONE && __double_as_longlong(tvm) == ONE &&
-                                        __double_as_longlong(to) == ONE)) {
+            if (__all_sync(CG_FULL, ku >= __double_as_longlong(mp[BD_KEXC]))) {
                 // excited tissue: every switch is 1
                 double unused;
                 const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], unused);
@@ -557,6 +567,10 @@ template <bool TH> struct BocfModel {
                 return;
             }
         }
+        const double tv = clamp01_int(fma(k, u, mp[BD_CV]));
+        const double tw = clamp01_int(fma(k, u, mp[BD_CW]));
+        const double tvm = clamp01_int(fma(k, u, mp[BD_CVM]));
+        const double to = clamp01_int(fma(k, u, mp[BD_CO]));
         const double Hv = (tv * tv) * fma(-2.0, tv, 3.0);
         const double Hw = (tw * tw) * fma(-2.0, tw, 3.0);
         const double Hvm = (tvm * tvm) * fma(-2.0, tvm, 3.0);

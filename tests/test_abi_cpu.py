@@ -140,3 +140,11 @@ def test_checked_build_loads_and_exports(L):
             "sys.exit(0 if _lib.lib().cg_bounds_checked() == 1 else 3)")
     env = dict(os.environ, CG_BOUNDS_CHECK="1")
     assert subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env).returncode == 0
+
+
+def test_bocf_sharpness_must_be_positive(L):
+    from paper_1309_1720_gb300 import Problem, BOCF, default_params
+    prm = default_params(BOCF)
+    prm[28] = 0.0
+    st, msg = _create(Problem(model=BOCF, dx=0.03, dt=0.05, params=prm))
+    assert st == 1 and "sharpness" in msg
