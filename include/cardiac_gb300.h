@@ -258,6 +258,13 @@ cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_out_host,
  * precedence), CG_OK otherwise. */
 cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags);
 
+/* The same for the latest run issued with this plan (cg_run, cg_batch_run,
+ * cg_rhs, the tangent-linear, adjoint and Newton calls): the plan records the
+ * workspace and stream of each run it issues.  flags = 0 and CG_OK when the
+ * plan has not run yet.  With one plan used on several streams at once, the
+ * latest issue wins; use cg_read_status with an explicit workspace there. */
+cg_status cg_get_device_status(cg_plan plan, uint32_t *flags);
+
 /* ------------------------------------------------- tangent-linear model */
 
 /* The paper's motivation (Sect. 1) is matrix-free Newton-Krylov solvers that

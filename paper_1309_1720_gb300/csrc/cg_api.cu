@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -154,6 +155,11 @@ struct cg_plan_s {
     int2 *d_deps = nullptr;
     int32_t sync_mode = cgk::SYNC_GRID;
     double *d_tab = nullptr;         // 2^(j/256) table of the exponential
+    // workspace and stream of the latest run issued with this plan (for
+    // cg_get_device_status; the plan's numerical content stays immutable)
+    std::mutex last_mu;
+    const void *last_ws = nullptr;
+    void *last_stream = nullptr;
 };
 
 namespace cgk {
@@ -166,6 +172,14 @@ void exp_table(double *tab, int n)
 }  // namespace cgk
 
 namespace {
+
+// Remember the workspace and stream of a run for cg_get_device_status.
+void note_run(cg_plan P, const void *ws, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> g(P->last_mu);
+    P->last_ws = ws;
+    P->last_stream = reinterpret_cast<void *>(s);
+}
 
 const void *lookup_tb_kernel(int kmodel, int stencil, int scheme)
 {
@@ -1006,6 +1020,7 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
         pout[k] = tab ? zout_u[i] : z_out + plan->inst[k].off;
         any_alias |= (pin[k] == pout[k]);
     }
+    note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     auto inst_bytes = [&](size_t k) {
@@ -1190,6 +1205,7 @@ CG_API cg_status cg_rhs(cg_plan plan, const double *z, double *f, void *workspac
     if (!k) return fail(CG_EUNSUPPORTED, "no kernel for this model/stencil");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(workspace);
+    note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     RunArgs a;
@@ -1260,6 +1276,23 @@ CG_API cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_ou
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(device to host)");
     uint32_t flags = 0;
     return cg_read_status(plan, workspace, stream, &flags);
+}
+
+CG_API cg_status cg_get_device_status(cg_plan plan, uint32_t *flags)
+{
+    if (!plan || !flags) return fail(CG_EINVAL, "NULL argument");
+    const void *ws;
+    void *stream;
+    {
+        std::lock_guard<std::mutex> g(plan->last_mu);
+        ws = plan->last_ws;
+        stream = plan->last_stream;
+    }
+    if (!ws) {
+        *flags = 0;
+        return CG_OK;
+    }
+    return cg_read_status(plan, ws, stream, flags);
 }
 
 CG_API cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint32_t *flags)
@@ -1397,6 +1430,7 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
     if (st != CG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(workspace);
+    note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     if (n_steps == 0) {
@@ -1459,6 +1493,7 @@ static cg_status tlm_linearized(cg_plan plan, const double *z0, double *zT, cons
     if (st != CG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(workspace);
+    note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     if (n_steps == 0) {
@@ -1580,6 +1615,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     double *kb = reinterpret_cast<double *>(ws + L.kb_off);
     double *part = reinterpret_cast<double *>(ws + L.part_off);
     const int nwarps = plan->nblocks * (plan->threads / 32);
+    note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nwarps * nd, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
