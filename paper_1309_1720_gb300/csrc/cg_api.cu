@@ -333,7 +333,8 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
         P.mp[cgk::KP_CV] = 0.5 - k * uv;
         P.mp[cgk::KP_6KA] = 6.0 * k * a / tv;
         P.mp[cgk::KP_M] = M;
-        P.mp[cgk::KP_MI] = (M >= 0 && M <= 64 && M == std::floor(M)) ? M : -1.0;
+        const int64_t mi = (M >= 0 && M <= 64 && M == std::floor(M)) ? (int64_t)M : -1;
+        std::memcpy(&P.mp[cgk::KP_MI], &mi, sizeof mi);
         P.mp[cgk::KP_TH] = (p.flags & CG_FLAG_TANH_AS_HK) ? 1.0 : 0.0;
         static_assert(cgk::KP_N <= cgk::NMP, "model constant table too small");
         I.mi[0] = I.wc[0] - 1.0 / tu;

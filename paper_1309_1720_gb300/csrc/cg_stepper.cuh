@@ -297,20 +297,24 @@ enum {
     KP_CV,      // 1/2 - k u_v
     KP_6KA,     // 6 k a/tau_v: d t_v/du = KP_6KA t (1 - t)
     KP_M,       // M
-    KP_MI,      // M if it is an integer in [0, 64], else -1
-    KP_TH,      // 1: tanh variant
+    KP_MI,      // bits of an int64: M if it is an integer in [0, 64], else -1
+    KP_TH,      // 1.0: tanh variant (tested by its bits, on the integer pipe)
     KP_N
 };
 
-// v^m for an integer m >= 1 by repeated squaring.
+// v^m for an integer m >= 1 by repeated squaring (M = 6: v^2, v^4, v^2 v^4).
 __device__ __forceinline__ double int_pow(double v, int m)
 {
+    while (!(m & 1)) {
+        v *= v;
+        m >>= 1;
+    }
     double r = v;
-    m -= 1;
-    while (m > 0) {
+    m >>= 1;
+    while (m) {
+        v *= v;
         if (m & 1) r *= v;
         m >>= 1;
-        if (m) v *= v;
     }
     return r;
 }
@@ -323,19 +327,15 @@ template <> struct Model<MODEL_KARMA> {
     struct Coef { double A_u; const double *tab; };    // A_u = wc_u - 1/tau_u
     __device__ static Coef coef(const Inst &I) { return Coef{I.mi[0], I.tab}; }
 
-    // v^M and, when JAC, M v^(M-1) (M = 0: 1 and 0).
+    // v^M and, when JAC, M v^(M-1) (M = 0: 1 and 0).  v^M is computed the
+    // same way with and without JAC, so both give the same values.
     template <bool JAC>
     __device__ __forceinline__ static double vpow(const double *mp, double v, double &dvm)
     {
-        const int mi = (int)mp[KP_MI];
-        if (mi >= 2) {
-            const double p1 = int_pow(v, mi - 1);
-            if constexpr (JAC) dvm = mp[KP_M] * p1;
-            return p1 * v;
-        }
-        if (mi == 1) {
-            if constexpr (JAC) dvm = 1.0;
-            return v;
+        const int mi = (int)__double_as_longlong(mp[KP_MI]);
+        if (mi >= 1) {
+            if constexpr (JAC) dvm = (mi >= 2) ? mp[KP_M] * int_pow(v, mi - 1) : 1.0;
+            return int_pow(v, mi);
         }
         if (mi == 0) {
             if constexpr (JAC) dvm = 0.0;
@@ -351,7 +351,7 @@ template <> struct Model<MODEL_KARMA> {
     {
         const double u = z[0], v = z[1];
         double sig, dsig = 0.0;
-        if (mp[KP_TH] != 0.0) {
+        if (__double_as_longlong(mp[KP_TH]) != 0) {
             const double th = clamp01_int(fma(-1.0 / 3.0, u, mp[KP_HA]));
             sig = (th * th) * fma(-2.0, th, 3.0);
             if constexpr (JAC) dsig = -2.0 * (th * (1.0 - th));
