@@ -299,7 +299,9 @@ cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, double *
  * must not be touched between the two calls; the plan, n_steps and the
  * workspace pointer must be the same in both.  Layouts and in-place rules as
  * cg_tlm_run.  CG_EINVAL for NULL buffers, negative counts, a misaligned
- * workspace or partial overlap; CG_EUNSUPPORTED for batch plans and the gate
+ * workspace, partial overlap, or (cg_tlm_apply) a workspace that the plan
+ * did not linearize over the same n_steps (the plan remembers its latest 16
+ * linearized workspaces); CG_EUNSUPPORTED for batch plans and the gate
  * integrators. */
 cg_status cg_tlm_linearized_workspace_size(cg_plan plan, int32_t n_tangents, int64_t n_steps, size_t *bytes);
 cg_status cg_tlm_linearize(cg_plan plan, const double *z0, double *zT, int64_t n_steps, void *workspace,

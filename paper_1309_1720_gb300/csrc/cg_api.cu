@@ -160,6 +160,9 @@ struct cg_plan_s {
     std::mutex last_mu;
     const void *last_ws = nullptr;
     void *last_stream = nullptr;
+    // workspaces linearized with this plan and their step counts (the latest
+    // 16), so that cg_tlm_apply can reject a workspace it never filled
+    std::vector<std::pair<const void *, int64_t>> linearized;
 };
 
 namespace cgk {
@@ -1490,6 +1493,20 @@ static cg_status tlm_linearized(cg_plan plan, const double *z0, double *zT, cons
     if (apply && n_tangents && overlaps(dz0, dzT, tbytes)) return fail(CG_EINVAL, "input and output partially overlap");
     if (plan->ns == 1 && n_steps > 0 && (apply ? (n_tangents && dz0 == dzT) : (z0 == zT)))
         return fail(CG_EINVAL, "in-place tangent-linear runs need a multi-stage scheme");
+    {
+        std::lock_guard<std::mutex> g(plan->last_mu);
+        auto &lin = plan->linearized;
+        auto it = std::find_if(lin.begin(), lin.end(), [&](const auto &r) { return r.first == workspace; });
+        if (apply) {
+            if (it == lin.end() || it->second != n_steps)
+                return fail(CG_EINVAL, "this workspace was not linearized with this plan over %lld steps",
+                            (long long)n_steps);
+        } else {
+            if (it != lin.end()) lin.erase(it);
+            if (lin.size() >= 16) lin.erase(lin.begin());
+            lin.emplace_back(workspace, n_steps);
+        }
+    }
     cg_status st = check_plan_device(plan);
     if (st != CG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

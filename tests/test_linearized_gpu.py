@@ -169,3 +169,26 @@ def test_periodic_orbit_linearized_same_iterates(cuda_ok):
     za, Ta, ha = periodic_orbit(base, z1, T0, n, max_newton=2, linearized=False)
     zb, Tb, hb = periodic_orbit(base, z1, T0, n, max_newton=2, linearized=True)
     assert torch.equal(za, zb) and Ta == Tb and ha == hb
+
+
+def test_apply_needs_a_linearized_workspace(cuda_ok):
+    """cg_tlm_apply refuses a workspace the plan never linearized, or one
+    linearized over another step count."""
+    import ctypes
+    import torch
+    from paper_1309_1720_gb300 import Plan, FHN, RK4, STENCIL5, _lib
+    L = _lib.lib()
+    plan = Plan(_prob(FHN, 40, 30, STENCIL5, RK4))
+    z0 = torch.from_numpy(_z0(FHN, 40, 30)).cuda()
+    dz = z0[None].clone()
+    sz = ctypes.c_size_t()
+    assert L.cg_tlm_linearized_workspace_size(plan.handle, 1, 5, ctypes.byref(sz)) == 0
+    ws = torch.zeros(int(sz.value), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(dz)
+    assert L.cg_tlm_apply(plan.handle, dz.data_ptr(), out.data_ptr(), 1, 5, ws.data_ptr(), None) == 1
+    zT = torch.empty_like(z0)
+    assert L.cg_tlm_linearize(plan.handle, z0.data_ptr(), zT.data_ptr(), 5, ws.data_ptr(), None) == 0
+    assert L.cg_tlm_apply(plan.handle, dz.data_ptr(), out.data_ptr(), 1, 4, ws.data_ptr(), None) == 1
+    assert L.cg_tlm_apply(plan.handle, dz.data_ptr(), out.data_ptr(), 1, 5, ws.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, plan.tlm(z0, dz, 5)[1])
