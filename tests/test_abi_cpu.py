@@ -128,9 +128,9 @@ def test_checked_build_loads_and_exports(L):
     replacement: same exported symbols, selected by CG_BOUNDS_CHECK=1."""
     import subprocess
     import sys
-    from paper_1309_1720_gb300 import build
+    from paper_1309_1720_gb300 import build, _lib
     build.build(checked=True)
-    assert L.cg_bounds_checked() == 0
+    assert L.cg_bounds_checked() == (1 if _lib.CHECKED else 0)
     chk = ctypes.CDLL(build.LIB_CHECKED)
     chk.cg_bounds_checked.restype = ctypes.c_int32
     assert chk.cg_bounds_checked() == 1

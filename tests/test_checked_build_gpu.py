@@ -17,8 +17,10 @@ ROOT = os.path.dirname(HERE)
 
 
 def test_checked_build_clean_and_bitwise_equal(cuda_ok, tmp_path):
-    from paper_1309_1720_gb300 import build
+    from paper_1309_1720_gb300 import build, _lib
     import checked_cases
+    if _lib.CHECKED:
+        pytest.skip("this process already runs the checked build")
     build.build(checked=True)
     npz = str(tmp_path / "checked.npz")
     env = dict(os.environ, CG_BOUNDS_CHECK="1")
@@ -26,7 +28,6 @@ def test_checked_build_clean_and_bitwise_equal(cuda_ok, tmp_path):
     r = subprocess.run([sys.executable, os.path.join(HERE, "checked_cases.py"), npz], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, (r.stdout[-4000:], r.stderr[-4000:])
-    from paper_1309_1720_gb300 import _lib
     assert _lib.lib().cg_bounds_checked() == 0
     plain = checked_cases.run_all()
     chk = np.load(npz)
