@@ -60,7 +60,8 @@ def parse():
                          "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
                          "16 steps (adj), or 200 steps of the 128^2 Euler problem with 4 steps per grid "
                          "barrier (c1)")
-    ap.add_argument("--experiment", default=None, choices=["all", "timing", "grid", "convergence", "orbit"],
+    ap.add_argument("--experiment", default=None,
+                    choices=["all", "timing", "grid", "convergence", "orbit", "snapshots"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
 
@@ -564,6 +565,60 @@ def paper_experiments(which):
         print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": gname, "steps": 2000,
                           "fit": "t = a max(1, (N/N0)^2), a = median of N <= 64, b = a/N0^2 = median t/N^2 "
                                  "for N >= 2048", "results": res}), flush=True)
+    if which in ("all", "snapshots"):
+        # Fig. 2: voltage fields of the three models on the paper's grids
+        # (FHN 384^2, Karma 256^2, BOCF 768^2), RK4, reported as the range of
+        # u over the run (the paper quotes about (-1, 1), (0, 3.5) and
+        # (0, 1.55)) and whether activity is self-sustained at the end.  FHN
+        # and BOCF start from the seeded states; Karma from an S1-S2 cross
+        # field stimulus (a plane wave from the left edge, then the lower
+        # half stimulated at 300 ms, exciting only recovered tissue), which
+        # leaves a rotating spiral: its period is measured from the
+        # upcrossings of u at the domain's centre over the last third.
+        snaps = {
+            "fhn": (api.Problem(model=api.FHN, nx=384, ny=384, dx=0.04, scheme=api.RK4, dt=2e-4),
+                    I.fhn_broken_wave(384, 384, seed=0), 200.0, 0.0, None, 1.0),
+            "karma": (api.Problem(model=api.KARMA, nx=256, ny=256, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,),
+                                  scheme=api.RK4, dt=0.05), np.zeros((2, 256, 256)), 3000.0, 1.0, 300.0, 1.0),
+            "bocf": (api.Problem(model=api.BOCF, nx=768, ny=768, dx=0.03, D=(1.171e-3,), scheme=api.RK4,
+                                 dt=0.05), I.bocf_spiral_cores(768, 768, seed=0), 2000.0, 0.5, None, 5.0),
+        }
+        res = {}
+        for name, (prob, z0, T, thr, t_s2, every) in snaps.items():
+            plan = Plan(prob)
+            n = prob.nx
+            z = torch.from_numpy(np.ascontiguousarray(z0)).cuda()
+            if t_s2 is not None:
+                z[0, :, :10] = 3.0                                   # S1
+                z = plan.run(z, int(round(t_s2 / prob.dt)))
+                z[0, : n // 2, :] = 3.0                              # S2
+                t0 = t_s2
+            else:
+                t0 = 0.0
+            n_chunk = int(round(every / prob.dt))                  # one sample per `every` time units
+            chunks = int(round((T - t0) / prob.dt / n_chunk))
+            umin, umax, excited, probe = float("inf"), -float("inf"), [], []
+            for _ in range(chunks):
+                z = plan.run(z, n_chunk)
+                u = z[0]
+                umin = min(umin, float(u.min()))
+                umax = max(umax, float(u.max()))
+                excited.append(float((u > thr).double().mean()))
+                probe.append(float(u[n // 2, n // 2]))
+            plan.status()
+            last = max(2, chunks // 3)                              # the last third of the run
+            tail_exc = excited[-last:]
+            pr = np.array(probe[-last:])
+            ups = np.nonzero((pr[:-1] <= thr) & (pr[1:] > thr))[0]
+            period = float(np.mean(np.diff(ups)) * n_chunk * prob.dt) if len(ups) >= 3 else None
+            res[name] = {"grid": [prob.nx, prob.ny], "T": T, "u_min": umin, "u_max": umax,
+                         "excited_fraction_final": excited[-1],
+                         "excited_fraction_range_last_third": [min(tail_exc), max(tail_exc)],
+                         "self_sustained": bool(min(tail_exc) > 0.05),
+                         "probe_upcrossings_last_third": int(len(ups)), "rotation_period": period,
+                         "initial_state": "S1-S2 cross field" if t_s2 is not None else "seeded"}
+            plan.close()
+        print(json.dumps({"experiment": "voltage fields (Fig. 2)", "results": res}), flush=True)
     if which in ("all", "orbit"):
         # Sect. 1's use: a periodic orbit by Newton-Krylov.  A FitzHugh-Nagumo
         # pulse travelling round a periodic ring (512 x 2 cells, dx = 0.5)
