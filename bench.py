@@ -54,9 +54,10 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-case", nargs="?", const="fhn", default=None,
-                    choices=["fhn", "bocf", "tlm", "adj", "c1"],
+                    choices=["fhn", "bocf", "karma", "tlm", "adj", "c1"],
                     help="run a short case twice and exit (for ncu captures): 20 steps of the "
-                         "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), or on "
+                         "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), 10 steps "
+                         "of the 2048^2 Karma model (karma), or on "
                          "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
                          "16 steps (adj), or 200 steps of the 128^2 Euler problem with 4 steps per grid "
                          "barrier (c1)")
@@ -763,6 +764,15 @@ def main():
             z0 = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
             out = torch.empty_like(z0)
             steps = 2
+        elif args.profile_case == "karma":
+            # Karma 2048^2 5-point RK4 (the launch shape its bench row uses)
+            n = 2048
+            kp = api.Problem(model=api.KARMA, nx=n, ny=n, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,), scheme=api.RK4,
+                             dt=0.05)
+            plan = autotune.plan_for([kp], autotune.cached([kp]))
+            z0 = torch.from_numpy(I.karma_broken_wave(n, n, seed=0)).cuda()
+            out = torch.empty_like(z0)
+            steps = 10
         else:
             steps = 20
         for _ in range(2):
