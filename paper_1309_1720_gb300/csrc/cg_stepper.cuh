@@ -789,11 +789,12 @@ __device__ __forceinline__ void row_sums(int lane, const double (&v)[CX], double
 // reads its state from store[k*NS] and its stage inputs from store[k*NS + s]
 // and writes store[(k+1)*NS] (states of NV planes each), so that the
 // adjoint sweep can revisit them.
+// (no default member initializers: the type also lives in shared memory)
 struct Bufs {
     const double *zin;
     double *zout;
     double *blk;
-    double *store = nullptr;
+    double *store;
 };
 
 // Buffers of instance i (plan order): its slice of the packed state, or the

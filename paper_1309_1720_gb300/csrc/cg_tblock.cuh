@@ -9,9 +9,12 @@
 // in shared memory, the region it updates shrinking by one cell per stage (a
 // stage reads one ring of neighbours), and written back: one grid barrier
 // per K steps instead of one per stage, at the price of recomputing the halo.
-// Ghost points (Fig. 1) at the domain's edges are refilled from the cells
-// they mirror after every stage, so the shrinking region never needs values
-// from another tile between barriers.
+// Ghost points (Fig. 1) at the domain's edges are loaded from the cells
+// they mirror (or repeat), and at each stage a region that reaches an edge
+// also computes its ghost ring, every ghost evaluated as its source cell
+// (same inputs, hence the same value): the shrinking region never needs
+// values from another tile between barriers, and no stage needs a separate
+// ghost refill.
 //
 // Each cell's arithmetic is the stage kernel's: the model's local terms with
 // the centre weight folded in, the off-centre sums in the same order (5-point:
@@ -62,7 +65,6 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
     __shared__ Inst s_inst;
     int cur = -1;                            // instance held in s_inst (the same in every thread)
     const int bc = a.bc;
-    const bool mirror = (bc == CG_BC_MIRROR);
     const int Hmax = t.k * NS;
     const int WS = t.wmax;
     // arrays (each NV planes of WS): NS == 1: YA, YB; else Z, ACC, YA, YB
@@ -155,49 +157,6 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
         const double *src = (p == 0) ? c.zin : tb_dst(c.zout, c.scr, alias, p - 1, P);
         double *dst = tb_dst(c.zout, c.scr, alias, p, P);
 
-        // Ghost points of buffer B on the region [xl, xh) x [yl, yh): x
-        // ghosts of its rows first, then whole y-ghost rows (corners
-        // follow both flips).
-        auto fill_ghosts = [&](double *B, int xl, int xh, int yl, int yh) {
-            const int gx_lo = mirror ? 1 : 0, gx_hi = mirror ? nx - 2 : nx - 1;
-            const int gy_lo = mirror ? 1 : 0, gy_hi = mirror ? ny - 2 : ny - 1;
-            const bool left = (xl == 0), right = (xh == nx), bot = (yl == 0), top = (yh == ny);
-            if (!(left || right || bot || top)) return;    // block-uniform: interior tiles skip both syncs
-            const int nrow = yh - yl;
-            for (int q = threadIdx.x; q < 2 * nrow; q += blockDim.x) {
-                const int y = yl + (q >> 1);
-                const bool lft = (q & 1) == 0;
-                if (lft ? !left : !right) continue;
-                if constexpr (BOUNDS_CHECK) {
-                    if (!in_window(lft ? -1 : nx, y) || !in_window(lft ? gx_lo : gx_hi, y)) {
-                        bad |= CG_DEV_BOUNDS;
-                        continue;
-                    }
-                }
-                const int d = at(lft ? -1 : nx, y), sidx = at(lft ? gx_lo : gx_hi, y);
-#pragma unroll
-                for (int f = 0; f < NV; ++f) B[f * WS + d] = B[f * WS + sidx];
-            }
-            __syncthreads();
-            const int cl = left ? xl - 1 : xl, ch = right ? xh + 1 : xh;
-            const int ncol = ch - cl;
-            for (int q = threadIdx.x; q < 2 * ncol; q += blockDim.x) {
-                const int x = cl + (q >> 1);
-                const bool lo = (q & 1) == 0;
-                if (lo ? !bot : !top) continue;
-                if constexpr (BOUNDS_CHECK) {
-                    if (!in_window(x, lo ? -1 : ny) || !in_window(x, lo ? gy_lo : gy_hi)) {
-                        bad |= CG_DEV_BOUNDS;
-                        continue;
-                    }
-                }
-                const int d = at(x, lo ? -1 : ny), sidx = at(x, lo ? gy_lo : gy_hi);
-#pragma unroll
-                for (int f = 0; f < NV; ++f) B[f * WS + d] = B[f * WS + sidx];
-            }
-            __syncthreads();
-        };
-
         // checked build: a window that does not fit its arrays skips every
         // access of this tile (the block still joins the grid barriers)
         const bool tb_ok = !BOUNDS_CHECK || (win_fits && WX >= 3 && gy1 - gy0 >= 3);
@@ -205,24 +164,27 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             bad |= CG_DEV_BOUNDS;
             return;
         }
-        // load the window's domain cells: the tile plus H cells of halo
+        // load the window: the tile plus H cells of halo and, where that
+        // reaches the domain's edge, the ghost points (read from the cells
+        // they mirror or repeat)
         {
             const int xl = max(x0 - H, 0), xh = min(x1 + H, nx), yl = max(y0 - H, 0), yh = min(y1 + H, ny);
-            const int w = xh - xl, n = w * (yh - yl);
+            const int exl = xl - (xl == 0), exh = xh + (xh == nx), eyl = yl - (yl == 0), eyh = yh + (yh == ny);
+            const int w = exh - exl, n = w * (eyh - eyl);
             for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const int gx = xl + c % w, gy = yl + c / w;
+                const int gx = exl + c % w, gy = eyl + c / w;
+                const int sx = map_idx(gx, nx, bc), sy = map_idx(gy, ny, bc);
                 if constexpr (BOUNDS_CHECK) {
-                    if (!in_window(gx, gy) || gx < 0 || gx >= nx || gy < 0 || gy >= ny || bad_ptr(src)) {
+                    if (!in_window(gx, gy) || sx < 0 || sx >= nx || sy < 0 || sy >= ny || bad_ptr(src)) {
                         bad |= CG_DEV_BOUNDS;
                         continue;
                     }
                 }
 #pragma unroll
                 for (int f = 0; f < NV; ++f)
-                    Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)gy * nx + gx);
+                    Z[f * WS + at(gx, gy)] = __ldcg(src + f * plane + (int64_t)sy * nx + sx);
             }
             __syncthreads();
-            fill_ghosts(Z, xl, xh, yl, yh);
         }
         double *Yin = Z;
         for (int g = 1; g <= H; ++g) {
@@ -230,7 +192,15 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             const bool last = (s == NS - 1);
             const int rad = H - g;
             const int xl = max(x0 - rad, 0), xh = min(x1 + rad, nx), yl = max(y0 - rad, 0), yh = min(y1 + rad, ny);
-            const int w = xh - xl, n = w * (yh - yl);
+            // Where the region reaches the domain's edge it takes in the
+            // ghost ring, each ghost computed as the cell it mirrors (same
+            // inputs, same value), so no refill is needed; not at the pass's
+            // last stage, which nothing reads.  A ghost's source is at most
+            // two cells in, inside the previous stage's region.
+            const bool gr = g < H;
+            const int exl = xl - (gr && xl == 0), exh = xh + (gr && xh == nx);
+            const int eyl = yl - (gr && yl == 0), eyh = yh + (gr && yh == ny);
+            const int w = exh - exl, n = w * (eyh - eyl);
             double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
             const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
             // every thread runs the same number of iterations, so the
@@ -240,36 +210,38 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
                 const int c = base + (int)threadIdx.x;
                 const bool act = c < n;
                 const int cc = act ? c : n - 1;
-                const int gx = xl + cc % w, gy = yl + cc / w;
-                int li = at(gx, gy);
+                const int gx = exl + cc % w, gy = eyl + cc / w;
+                const int sx = map_idx(gx, nx, bc), sy = map_idx(gy, ny, bc);   // identity inside the grid
+                int li = at(gx, gy), ls = at(sx, sy);
                 bool act_ok = act;
                 if constexpr (BOUNDS_CHECK) {
-                    // the cell and its eight neighbours inside the window;
-                    // a failed check computes a harmless interior cell
-                    // instead and stores nothing (whole warps stay)
-                    if (!(in_window(gx - 1, gy - 1) && in_window(gx + 1, gy + 1))) {
+                    // the slot, the source cell and its eight neighbours
+                    // inside the window; a failed check computes a harmless
+                    // interior cell instead and stores nothing (whole warps
+                    // stay)
+                    if (!(in_window(gx, gy) && in_window(sx - 1, sy - 1) && in_window(sx + 1, sy + 1))) {
                         bad |= CG_DEV_BOUNDS;
-                        li = WX + 1;
+                        li = ls = WX + 1;
                         act_ok = false;
                     }
                 }
                 double zc[NV];
 #pragma unroll
-                for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + li];
+                for (int f = 0; f < NV; ++f) zc[f] = Yin[f * WS + ls];
                 double F[NV];
                 MD::local(coef, mp, zc, F);
 #pragma unroll
                 for (int f = 0; f < ND; ++f) {
                     const double *Q = Yin + f * WS;
-                    const double Wv = Q[li - 1], Ev = Q[li + 1];
+                    const double Wv = Q[ls - 1], Ev = Q[ls + 1];
                     if (ST == CG_STENCIL9) {
-                        const double Rl = Q[li - WX - 1] + Q[li - WX + 1];
-                        const double Rh = Q[li + WX - 1] + Q[li + WX + 1];
-                        const double Tl = fma(wt[f], Q[li - WX], Rl), Th = fma(wt[f], Q[li + WX], Rh);
+                        const double Rl = Q[ls - WX - 1] + Q[ls - WX + 1];
+                        const double Rh = Q[ls + WX - 1] + Q[ls + WX + 1];
+                        const double Tl = fma(wt[f], Q[ls - WX], Rl), Th = fma(wt[f], Q[ls + WX], Rh);
                         const double acc_f = fma(wd[f], Tl + Th, F[f]);
                         F[f] = fma(wx[f], Wv + Ev, acc_f);
                     } else {
-                        double acc_f = fma(wy[f], Q[li - WX] + Q[li + WX], F[f]);
+                        double acc_f = fma(wy[f], Q[ls - WX] + Q[ls + WX], F[f]);
                         F[f] = fma(wx[f], Wv + Ev, acc_f);
                     }
                 }
@@ -292,7 +264,6 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
                 }
             }
             __syncthreads();
-            fill_ghosts(Yout, xl, xh, yl, yh);
             Yin = Yout;
         }
         // write the tile back

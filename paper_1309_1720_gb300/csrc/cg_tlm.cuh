@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
         const int64_t step = g / NS;
         double *jb = t.jbuf + g * t.jstride;
         if (!t.skip_primal) {
-            const Bufs Bp{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off};
+            const Bufs Bp{a.z_in + I.off, a.z_out + I.off, a.ws + I.ws_off, nullptr};
             for (int k = sbeg; k < send; ++k) {
                 const Seg sg = seg_k(k);
                 bad |= SP::seg(a, I, mp, Bp, jb, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1, sg.mrow_b,
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(512, 1) k_tlm(const RunArgs a, const TlmArgs t
             }
         }
         for (int q = 0; q < t.n_tan; ++q) {
-            const Bufs Bt{t.dz_in + q * t.tstride, t.dz_out + q * t.tstride, t.tws + q * t.tblk};
+            const Bufs Bt{t.dz_in + q * t.tstride, t.dz_out + q * t.tstride, t.tws + q * t.tblk, nullptr};
             for (int k = sbeg; k < send; ++k) {
                 const Seg sg = seg_k(k);
                 bad |= STn::seg(a, I, mp, Bt, jb, sg.x0, sg.y0, sg.y1, sg.mrow_a, sg.ma0, sg.ma1,
