@@ -42,7 +42,7 @@ BYTES_PER_CELL_UPDATE = 32
 # dram__bytes_write.sum) on a 20-step launch of this workload; traffic grows
 # in proportion to the steps of a launch (L2 write-backs of the resident
 # working set), so one bench launch moves this times its cell-updates.
-MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 38.8
+MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 37.3
 
 
 def parse():
