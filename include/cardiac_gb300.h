@@ -261,8 +261,9 @@ cg_status cg_read_status(cg_plan plan, const void *workspace, void *stream, uint
 /* The same for the latest run issued with this plan (cg_run, cg_batch_run,
  * cg_rhs, the tangent-linear, adjoint and Newton calls): the plan records the
  * workspace and stream of each run it issues.  flags = 0 and CG_OK when the
- * plan has not run yet.  With one plan used on several streams at once, the
- * latest issue wins; use cg_read_status with an explicit workspace there. */
+ * plan has not run yet.  The workspace of that run must still be allocated.
+ * With one plan used on several streams at once, the latest issue wins; use
+ * cg_read_status with an explicit workspace there. */
 cg_status cg_get_device_status(cg_plan plan, uint32_t *flags);
 
 /* ------------------------------------------------- tangent-linear model */
