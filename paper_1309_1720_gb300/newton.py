@@ -12,8 +12,8 @@ dt = T / n_steps, by Newton's method on the bordered system
 shift along the orbit; F(Phi_T z) is dPhi_T/dT of the continuous flow).
 Each Newton step solves it by restarted GMRES with modified Gram-Schmidt.
 Every vector operation runs in the library's kernels: J v by the
-tangent-linear run (exact, not a difference of nearby solutions; by default
-from the stage Jacobians one linearizing run keeps per iterate), F by
+tangent-linear run (exact, not a difference of nearby solutions; from the
+stage Jacobians one linearizing run keeps per iterate when they fit), F by
 cg_rhs, inner products by cg_dot (fixed summation order) and updates by
 cg_axpby; only the (m+1) x m Hessenberg least-squares problem and the
 bordering scalars live on the host.
@@ -58,7 +58,7 @@ def _givens(a: float, b: float):
 
 def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: int, tol: float = 1e-11,
                    max_newton: int = 12, restart: int = 30, max_restarts: int = 4, gmres_rtol: float = 1e-7,
-                   linearized: bool = True, verbose: bool = False):
+                   linearized: Optional[bool] = None, verbose: bool = False):
     """Newton-Krylov search for a periodic orbit through (z0, T0).
 
     ``problem`` is a single-instance problem whose ``dt`` is ignored (each
@@ -66,7 +66,8 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
     keeps the stage Jacobians of its trajectory (n_steps x stages x NJ
     planes of device memory) so that every J v advances the tangent alone;
     otherwise each J v re-runs the primal.  Both give the same iterates bit
-    for bit.  Returns (z, T, history) with history a list of dicts (Newton
+    for bit; None (the default) linearizes when that store takes at most
+    half of the free device memory.  Returns (z, T, history) with history a list of dicts (Newton
     iteration, relative residual |Phi_T(z) - z| / |z|, T, GMRES iterations,
     final GMRES relative residual).
     """
@@ -79,6 +80,13 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
 
     def plan_for(T_):
         return api.Plan(replace(problem, dt=T_ / n_steps))
+
+    if linearized is None:
+        probe = plan_for(T)
+        sz = ctypes.c_size_t()
+        _lib.check(_lib.lib().cg_tlm_linearized_workspace_size(probe.handle, 1, int(n_steps), ctypes.byref(sz)))
+        probe.close()
+        linearized = sz.value <= torch.cuda.mem_get_info()[0] // 2
 
     for it in range(max_newton + 1):
         plan = plan_for(T)
