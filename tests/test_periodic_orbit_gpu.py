@@ -4,7 +4,6 @@ after one period.  Checks: Newton converges (quadratically at the end) to a
 relative residual |Phi_T(z) - z| / |z| below 1e-11, and the oracle, stepping
 the converged state independently, confirms the orbit; also cg_rhs against
 the oracle's right-hand side."""
-import math
 
 import numpy as np
 import pytest

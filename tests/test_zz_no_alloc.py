@@ -4,9 +4,7 @@ allocator, in allocation-free real-time loops).  Its scratch is a fixed
 static device array; the result must equal cg_run's with a caller
 workspace, call after call.  This file sorts last so that a run stopping at
 the first failure has already run every other test."""
-import ctypes
 
-import numpy as np
 import pytest
 
 from helpers import field_rel_err
