@@ -398,6 +398,14 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     torch.cuda.synchronize()
     t_adj = e0.elapsed_time(e1) / 1e3
     plan.status()
+    # dL/dz0 alone (no dL/dD accumulation)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.adjoint(z, lamT, T, with_dD=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_adj_state = e0.elapsed_time(e1) / 1e3
+    plan.status()
     # the same gradient keeping every stage input of the whole horizon in
     # HBM (one segment: no checkpoint sweep, no recomputation)
     import ctypes
@@ -439,6 +447,7 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         "adjoint_gcups": n * n * T / t_adj / 1e9,
         "adjoint_seconds_T2000": t_adj,
         "adjoint_vs_plain": (n * n * T / t_adj / 1e9) / g_plain,
+        "adjoint_state_only_seconds_T2000": t_adj_state,
         "adjoint_seconds_T2000_all_stages_stored": t_adj_all,
         "adjoint_all_stages_workspace_gb": sz.value / 1e9,
         "adjoint_all_stages_vs_plain": (n * n * T / t_adj_all / 1e9) / g_plain,
@@ -448,7 +457,7 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         "newton_gmres30_linearized_seconds": t_newton_lin,
         "newton_gmres30_linearized_bitwise_equal": newton_same,
         "note": "tlm: 64 tangents x 200 steps (rate); adjoint: full T = 2000 with ceil(sqrt(T)) checkpoints "
-                "(forward + segment recompute + reverse sweep), and with every stage input of the horizon "
+                "(forward + segment recompute + reverse sweep; state_only: dL/dz0 without dL/dD), and with every stage input of the horizon "
                 "kept in HBM (forward with stores + reverse sweep); newton: one GMRES(30) cycle on the "
                 "T = 2000 flow map (wall time, 30 exact JVPs of 2000 steps each; linearized: stage "
                 "Jacobians stored by one primal run, JVPs advance the tangent alone)"}

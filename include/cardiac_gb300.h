@@ -330,7 +330,9 @@ cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t check
  * is recomputed keeping every RK stage input and swept back with the
  * adjoint stage kernel (transposed stencil W L W^-1 under MIRROR ghosts,
  * transposed local Jacobian).  Cost: two forward runs plus one adjoint run.
- * dL/dD partial sums are reduced in a fixed order (bitwise reproducible). */
+ * dL/dD partial sums are reduced in a fixed order (bitwise reproducible).
+ * dLdD may be NULL: the run then skips the dL/dD dot products and their
+ * reduction (state-only gradients) and writes the same lam0 bit for bit. */
 cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
                          int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream);
 

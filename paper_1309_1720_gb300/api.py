@@ -254,10 +254,12 @@ class Plan:
         return Linearization(self, z0, n_steps, max_tangents, stream)
 
     def adjoint(self, z0: torch.Tensor, lamT: torch.Tensor, n_steps: int, checkpoint_every: int = 0,
-                stream=None):
+                stream=None, with_dD: bool = True):
         """Reverse-mode derivative of the n-step flow map: returns
         (lam0, dLdD) with lam0 = dL/dz0 for lamT = dL/dzT and dLdD the
-        derivatives w.r.t. each diffusive field's D (device tensors)."""
+        derivatives w.r.t. each diffusive field's D (device tensors).
+        ``with_dD=False`` skips the dL/dD accumulation (dLdD is None; lam0
+        is the same bit for bit)."""
         assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
         assert lamT.is_cuda and lamT.dtype == torch.float64 and lamT.is_contiguous()
         sz = ctypes.c_size_t()
@@ -266,8 +268,9 @@ class Plan:
             self._ws = torch.empty(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
         lam0 = torch.empty_like(lamT)
         nd = 2 if self.model == FHN else 1
-        dLdD = torch.empty(nd, dtype=torch.float64, device="cuda")
-        check(_lib.lib().cg_adjoint_run(self._h, z0.data_ptr(), lamT.data_ptr(), lam0.data_ptr(), dLdD.data_ptr(),
+        dLdD = torch.empty(nd, dtype=torch.float64, device="cuda") if with_dD else None
+        check(_lib.lib().cg_adjoint_run(self._h, z0.data_ptr(), lamT.data_ptr(), lam0.data_ptr(),
+                                        dLdD.data_ptr() if with_dD else None,
                                         int(n_steps), int(checkpoint_every), self._ws.data_ptr(),
                                         _stream_handle(stream)))
         return lam0, dLdD

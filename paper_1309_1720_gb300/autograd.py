@@ -3,9 +3,9 @@
 ``CGFlow.apply(z0, D, plan, n_steps, checkpoint_every)`` returns z(T) from the
 CUDA stepper; its backward calls the discrete adjoint kernels with
 sqrt(T)-checkpointed recomputation (cg_adjoint_run), giving dL/dz0 and dL/dD
-for each diffusive field's D (anisotropy ratio fixed).  ``D`` must hold the
-diffusivities the plan was built with; it is an input only so that autograd
-can route its gradient.
+for each diffusive field's D (anisotropy ratio fixed; skipped when D does
+not require a gradient).  ``D`` must hold the diffusivities the plan was
+built with; it is an input only so that autograd can route its gradient.
 """
 from __future__ import annotations
 
@@ -27,8 +27,10 @@ class CGFlow(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_zT):
         (z0,) = ctx.saved_tensors
-        lam0, dLdD = ctx.plan.adjoint(z0, grad_zT.detach().contiguous(), ctx.n_steps, ctx.every)
-        return lam0, dLdD.reshape(ctx.d_shape), None, None, None
+        want_dD = ctx.needs_input_grad[1]
+        lam0, dLdD = ctx.plan.adjoint(z0, grad_zT.detach().contiguous(), ctx.n_steps, ctx.every,
+                                      with_dD=want_dD)
+        return lam0, dLdD.reshape(ctx.d_shape) if want_dD else None, None, None, None
 
 
 def flow(z0: torch.Tensor, D: torch.Tensor, plan, n_steps: int, checkpoint_every: int = 0) -> torch.Tensor:

@@ -32,6 +32,7 @@ struct AdjArgs {
     double *lam;           // lambda: in dL/dz_{k+1}, out dL/dz_k
     double *lacc;          // running sum lam + sum Yb_s
     double *partial;       // [warps][ND] dL/dD partial sums (accumulated over launches)
+    int32_t want_dd;       // nonzero: accumulate dL/dD (else partial is not touched)
     int64_t m;             // steps of this segment
     int64_t r0;            // reverse stage counter at this segment's first reverse stage
 };
@@ -226,8 +227,10 @@ struct Adjoint {
                 for (int c = 0; c < CX; ++c) {
                     const double Sw = So[c];
                     F[c][f] += Sw;
-                    const double lt = fma(wcf[f], kc[c][f], Sw);        // ((D L)^T kbar)_f at the cell
-                    if (own & (1u << c)) dd[f] = fma(yc[c][f], lt, dd[f]);
+                    if (b.want_dd) {                                    // kernel argument: warp-uniform
+                        const double lt = fma(wcf[f], kc[c][f], Sw);    // ((D L)^T kbar)_f at the cell
+                        if (own & (1u << c)) dd[f] = fma(yc[c][f], lt, dd[f]);
+                    }
                 }
             }
 
@@ -326,12 +329,14 @@ __global__ void __launch_bounds__(512, 1) k_adj(const RunArgs a, const AdjArgs b
     }
     if (!ok) return;
     // fixed-order warp reduction of the dL/dD partials, one slot per warp
+    if (b.want_dd) {
 #pragma unroll
-    for (int f = 0; f < ND; ++f) {
-        double v = dd[f];
+        for (int f = 0; f < ND; ++f) {
+            double v = dd[f];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CG_FULL, v, o);
-        if (lane == 0) b.partial[(int64_t)gw * ND + f] += v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CG_FULL, v, o);
+            if (lane == 0) b.partial[(int64_t)gw * ND + f] += v;
+        }
     }
     bad = __reduce_or_sync(CG_FULL, bad);
     if (lane == 0 && bad) atomicOr(a.status, bad);

@@ -1614,7 +1614,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
     if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
-    if (!z0 || !lamT || !lam0 || !dLdD || !workspace || n_steps < 0 || checkpoint_every < 0)
+    if (!z0 || !lamT || !lam0 || !workspace || n_steps < 0 || checkpoint_every < 0)
         return fail(CG_EINVAL, "bad argument");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
@@ -1635,8 +1635,10 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     const int nwarps = plan->nblocks * (plan->threads / 32);
     note_run(plan, ws, s);
     cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nwarps * nd, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
+    if (dLdD) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nwarps * nd, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (n_steps == 0) {
         if (lam0 != lamT) e = cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
@@ -1685,6 +1687,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
         b.lam = lam;
         b.lacc = lacc;
         b.partial = part;
+        b.want_dd = dLdD != nullptr;
         b.m = m;
         b.r0 = r;
         void *aargs[] = {&a, &b};
@@ -1695,6 +1698,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     // 4. outputs
     e = cudaMemcpyAsync(lam0, lam, sbytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam0)");
+    if (!dLdD) return CG_OK;
     cgk::Inv4 inv;
     for (int f = 0; f < 4; ++f) inv.v[f] = plan->dxx[f] != 0.0 ? 1.0 / plan->dxx[f] : 0.0;
     cgk::k_reduce_partials<<<1, 32, 0, s>>>(part, nwarps, nd, inv, dLdD);

@@ -170,3 +170,27 @@ def test_dLdD_bitwise_reproducible(cuda_ok):
     a0, d0 = plan.adjoint(z0, lamT, 30)
     a1, d1 = plan.adjoint(z0, lamT, 30)
     assert torch.equal(a0, a1) and torch.equal(d0, d1)
+
+
+@pytest.mark.parametrize("model,stencil", [(0, 1), (1, 1), (3, 0)])
+def test_state_only_adjoint_same_lam0(cuda_ok, model, stencil):
+    """Without dLdD the adjoint skips the dL/dD accumulation and its
+    reduction and returns the same dL/dz0 bit for bit, for every checkpoint
+    interval; autograd takes that path when D needs no gradient."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, RK4, autograd
+    p = _prob(model, 70, 45, stencil, RK4)
+    z0 = torch.from_numpy(_z0(p)).cuda()
+    lamT = torch.from_numpy(I.unit_direction(z0.shape, 5)).cuda()
+    plan = Plan(p)
+    lam = {}
+    for every in (0, 3, 12):
+        a0, d0 = plan.adjoint(z0, lamT, 12, checkpoint_every=every)
+        a1, d1 = plan.adjoint(z0, lamT, 12, checkpoint_every=every, with_dD=False)
+        assert d1 is None and d0.shape[0] >= 1
+        assert torch.equal(a0, a1)
+        lam[every] = a0
+    D = torch.zeros(d0.shape[0], dtype=torch.float64, device="cuda")     # no gradient wanted
+    z = z0.clone().requires_grad_(True)
+    autograd.flow(z, D, plan, 12).mul(lamT).sum().backward()
+    assert torch.equal(z.grad, lam[0])
