@@ -103,6 +103,24 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def _state(t, numel, name, cuda=True):
+    """``t`` if it is a contiguous float64 tensor on the device (host when
+    ``cuda`` is False) with ``numel`` elements (any count when None); raises
+    TypeError / ValueError otherwise.  The C ABI sees only pointers, so these
+    checks keep every kernel inside the buffers it is given."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64, got %s" % (name, t.dtype))
+    if bool(t.is_cuda) != cuda:
+        raise ValueError("%s must be a %s tensor" % (name, "CUDA" if cuda else "CPU"))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return t
+
+
 class Plan:
     """An immutable stepping plan for one instance or a packed batch."""
 
@@ -174,21 +192,24 @@ class Plan:
     def run(self, z_in: torch.Tensor, n_steps: int, out: Optional[torch.Tensor] = None,
             stream=None, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Advance by n_steps; returns ``out`` (allocated if None)."""
-        assert z_in.is_cuda and z_in.dtype == torch.float64 and z_in.is_contiguous()
-        assert z_in.numel() == self.offsets[-1], "state has %d elements, plan expects %d" % (
-            z_in.numel(), self.offsets[-1])
-        if out is None:
-            out = torch.empty_like(z_in)
-        ws = self.workspace() if workspace is None else workspace
+        _state(z_in, self.offsets[-1], "z_in")
+        out = torch.empty_like(z_in) if out is None else _state(out, self.offsets[-1], "out")
+        if workspace is None:
+            ws = self.workspace()
+        elif not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.is_contiguous()
+                  and workspace.numel() * workspace.element_size() >= self.workspace_bytes):
+            raise ValueError("workspace must be a contiguous CUDA tensor of at least %d bytes"
+                             % self.workspace_bytes)
+        else:
+            ws = workspace
         check(_lib.lib().cg_run(self._h, z_in.data_ptr(), out.data_ptr(), int(n_steps), ws.data_ptr(),
                                 _stream_handle(stream)))
         return out
 
     def rhs(self, z: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """F(z) = D L z + N[z], the right-hand side the steps integrate."""
-        assert z.is_cuda and z.dtype == torch.float64 and z.is_contiguous()
-        assert z.numel() == self.offsets[-1]
-        out = torch.empty_like(z) if out is None else out
+        _state(z, self.offsets[-1], "z")
+        out = torch.empty_like(z) if out is None else _state(out, self.offsets[-1], "out")
         check(_lib.lib().cg_rhs(self._h, z.data_ptr(), out.data_ptr(), self.workspace().data_ptr(),
                                 _stream_handle(stream)))
         return out
@@ -198,11 +219,15 @@ class Plan:
         shape [n_v, ny, nx]); returns the output tensors (``outs`` or new ones;
         ``outs[i] is states[i]`` steps in place)."""
         n = len(self.problems)
-        assert len(states) == n
+        if len(states) != n:
+            raise ValueError("%d states for a plan of %d instances" % (len(states), n))
         for i, z in enumerate(states):
-            assert z.is_cuda and z.dtype == torch.float64 and z.is_contiguous()
-            assert z.numel() == self.offsets[i + 1] - self.offsets[i]
+            _state(z, self.offsets[i + 1] - self.offsets[i], "states[%d]" % i)
         outs = [torch.empty_like(z) for z in states] if outs is None else list(outs)
+        if len(outs) != n:
+            raise ValueError("%d outputs for a plan of %d instances" % (len(outs), n))
+        for i, o in enumerate(outs):
+            _state(o, self.offsets[i + 1] - self.offsets[i], "outs[%d]" % i)
         pin = (ctypes.c_void_p * n)(*[z.data_ptr() for z in states])
         pout = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
         ws = self.workspace()
@@ -214,10 +239,8 @@ class Plan:
         """Advance a state held in host memory (a CPU float64 tensor, ideally
         pinned): copy in, step, copy out, wait.  Returns ``out`` (a CPU
         tensor, allocated if None; may be ``z_in``)."""
-        assert not z_in.is_cuda and z_in.dtype == torch.float64 and z_in.is_contiguous()
-        assert z_in.numel() == self.offsets[-1]
-        if out is None:
-            out = torch.empty_like(z_in)
+        _state(z_in, self.offsets[-1], "z_in", cuda=False)
+        out = torch.empty_like(z_in) if out is None else _state(out, self.offsets[-1], "out", cuda=False)
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_host_workspace_size(self._h, ctypes.byref(sz)))
         if self._host_ws is None or self._host_ws.numel() < sz.value:
@@ -237,12 +260,14 @@ class Plan:
             dzT: Optional[torch.Tensor] = None, stream=None):
         """Exact Jacobian-vector products of the n-step flow map: returns
         (zT, dzT) with dzT[i] = dPhi/dz(z0) dz0[i]; dz0 is [T, n_v, ny, nx]."""
-        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
-        assert dz0.is_cuda and dz0.dtype == torch.float64 and dz0.is_contiguous()
-        n_t = dz0.numel() // z0.numel()
-        assert n_t * z0.numel() == dz0.numel()
-        zT = torch.empty_like(z0) if zT is None else zT
-        dzT = torch.empty_like(dz0) if dzT is None else dzT
+        N = self.offsets[-1]
+        _state(z0, N, "z0")
+        _state(dz0, None, "dz0")
+        n_t = dz0.numel() // N
+        if n_t * N != dz0.numel():
+            raise ValueError("dz0 has %d elements, not a multiple of the state's %d" % (dz0.numel(), N))
+        zT = torch.empty_like(z0) if zT is None else _state(zT, N, "zT")
+        dzT = torch.empty_like(dz0) if dzT is None else _state(dzT, n_t * N, "dzT")
         ws = self.tlm_workspace(n_t)
         check(_lib.lib().cg_tlm_run(self._h, z0.data_ptr(), dz0.data_ptr(), zT.data_ptr(), dzT.data_ptr(),
                                     n_t, int(n_steps), ws.data_ptr(), _stream_handle(stream)))
@@ -260,8 +285,8 @@ class Plan:
         derivatives w.r.t. each diffusive field's D (device tensors).
         ``with_dD=False`` skips the dL/dD accumulation (dLdD is None; lam0
         is the same bit for bit)."""
-        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
-        assert lamT.is_cuda and lamT.dtype == torch.float64 and lamT.is_contiguous()
+        _state(z0, self.offsets[-1], "z0")
+        _state(lamT, self.offsets[-1], "lamT")
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_adjoint_workspace_size(self._h, int(n_steps), int(checkpoint_every), ctypes.byref(sz)))
         if self._ws is None or self._ws.numel() < sz.value:
@@ -281,7 +306,7 @@ class Plan:
         exact Jacobian-vector products (``linearized``: from stored stage
         Jacobians, no primal work per Krylov iteration; same result).
         Returns (dz, residual_history)."""
-        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        _state(z0, self.offsets[-1], "z0")
         L = _lib.lib()
         sz = ctypes.c_size_t()
         if linearized:
@@ -318,7 +343,7 @@ class Linearization:
     primal work (cg_tlm_apply), bit for bit the tangents of ``Plan.tlm``."""
 
     def __init__(self, plan: Plan, z0: torch.Tensor, n_steps: int, max_tangents: int = 1, stream=None):
-        assert z0.is_cuda and z0.dtype == torch.float64 and z0.is_contiguous()
+        _state(z0, plan.offsets[-1], "z0")
         self.plan = plan
         self.n_steps = int(n_steps)
         self.max_tangents = int(max_tangents)
@@ -332,10 +357,13 @@ class Linearization:
 
     def apply(self, dz0: torch.Tensor, dzT: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """dzT[i] = dPhi/dz(z0) dz0[i]; dz0 is [T, n_v, ny, nx] (or one state)."""
-        assert dz0.is_cuda and dz0.dtype == torch.float64 and dz0.is_contiguous()
-        n_t = dz0.numel() // self.zT.numel()
-        assert n_t * self.zT.numel() == dz0.numel() and n_t <= self.max_tangents
-        dzT = torch.empty_like(dz0) if dzT is None else dzT
+        N = self.zT.numel()
+        _state(dz0, None, "dz0")
+        n_t = dz0.numel() // N
+        if n_t * N != dz0.numel() or n_t > self.max_tangents:
+            raise ValueError("dz0 must hold 1..%d states of %d elements, got %d elements"
+                             % (self.max_tangents, N, dz0.numel()))
+        dzT = torch.empty_like(dz0) if dzT is None else _state(dzT, n_t * N, "dzT")
         check(_lib.lib().cg_tlm_apply(self.plan._h, dz0.data_ptr(), dzT.data_ptr(), n_t, self.n_steps,
                                       self.ws.data_ptr(), _stream_handle(stream)))
         return dzT

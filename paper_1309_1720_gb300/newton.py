@@ -71,7 +71,8 @@ def periodic_orbit(problem: api.Problem, z0: torch.Tensor, T0: float, n_steps: i
     iteration, relative residual |Phi_T(z) - z| / |z|, T, GMRES iterations,
     final GMRES relative residual).
     """
-    assert z0.is_cuda and z0.dtype == torch.float64
+    if not (isinstance(z0, torch.Tensor) and z0.is_cuda and z0.dtype == torch.float64):
+        raise TypeError("z0 must be a float64 CUDA tensor")
     vec = _Vec()
     z = z0.contiguous().clone().reshape(-1)
     shape = z0.shape
