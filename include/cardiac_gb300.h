@@ -46,6 +46,10 @@ extern "C" {
 
 #define CG_ABI_VERSION 1
 
+/* Largest n_steps (period_steps) any entry point accepts; larger counts, and
+ * workspace sizes that would not fit in 2^62 bytes, return CG_EINVAL. */
+#define CG_MAX_STEPS ((int64_t)1 << 56)
+
 typedef enum cg_status {
     CG_OK = 0,
     CG_EINVAL = 1,          /* invalid argument (message in cg_last_error) */

@@ -160,8 +160,10 @@ class Plan:
         return self._h
 
     def workspace(self) -> torch.Tensor:
+        """The plan's own device workspace (zero-filled when allocated, so its
+        status word reads 0 before the first run)."""
         if self._ws is None:
-            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda")
+            self._ws = torch.zeros(self.workspace_bytes, dtype=torch.uint8, device="cuda")
         return self._ws
 
     def close(self) -> None:
@@ -244,7 +246,7 @@ class Plan:
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_host_workspace_size(self._h, ctypes.byref(sz)))
         if self._host_ws is None or self._host_ws.numel() < sz.value:
-            self._host_ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+            self._host_ws = torch.zeros(int(sz.value), dtype=torch.uint8, device="cuda")
         check(_lib.lib().cg_run_host(self._h, z_in.data_ptr(), out.data_ptr(), int(n_steps),
                                      self._host_ws.data_ptr(), _stream_handle(stream)))
         return out
@@ -253,7 +255,7 @@ class Plan:
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_tlm_workspace_size(self._h, int(n_tangents), ctypes.byref(sz)))
         if self._ws is None or self._ws.numel() < sz.value:
-            self._ws = torch.empty(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+            self._ws = torch.zeros(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
         return self._ws
 
     def tlm(self, z0: torch.Tensor, dz0: torch.Tensor, n_steps: int, zT: Optional[torch.Tensor] = None,
@@ -290,7 +292,7 @@ class Plan:
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_adjoint_workspace_size(self._h, int(n_steps), int(checkpoint_every), ctypes.byref(sz)))
         if self._ws is None or self._ws.numel() < sz.value:
-            self._ws = torch.empty(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+            self._ws = torch.zeros(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
         lam0 = torch.empty_like(lamT)
         nd = 2 if self.model == FHN else 1
         dLdD = torch.empty(nd, dtype=torch.float64, device="cuda") if with_dD else None
@@ -313,7 +315,7 @@ class Plan:
             check(L.cg_newton_linearized_workspace_size(self._h, int(restart), int(period_steps), ctypes.byref(sz)))
         else:
             check(L.cg_newton_workspace_size(self._h, int(restart), ctypes.byref(sz)))
-        ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        ws = torch.zeros(int(sz.value), dtype=torch.uint8, device="cuda")
         dz = torch.empty_like(z0)
         hist = (ctypes.c_double * (restart * max_restarts + 1))()
         nit = ctypes.c_int32()
@@ -350,7 +352,7 @@ class Linearization:
         sz = ctypes.c_size_t()
         check(_lib.lib().cg_tlm_linearized_workspace_size(plan._h, self.max_tangents, self.n_steps,
                                                           ctypes.byref(sz)))
-        self.ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        self.ws = torch.zeros(int(sz.value), dtype=torch.uint8, device="cuda")
         self.zT = torch.empty_like(z0)
         check(_lib.lib().cg_tlm_linearize(plan._h, z0.data_ptr(), self.zT.data_ptr(), self.n_steps,
                                           self.ws.data_ptr(), _stream_handle(stream)))

@@ -25,6 +25,9 @@ using cgk::RunArgs;
 namespace {
 
 thread_local std::string g_err;
+// Longest run any entry point accepts: stage counters (n_steps x stages)
+// and per-step byte counts stay far from int64 / size_t overflow.
+constexpr int64_t MAX_STEPS = CG_MAX_STEPS;
 
 cg_status fail(cg_status st, const char *fmt, ...)
 {
@@ -1154,7 +1157,7 @@ CG_API cg_status cg_run(cg_plan plan, const double *z_in, double *z_out, int64_t
     cgk::NvtxRange nvtx_range("cg_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
-    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    if (n_steps < 0 || n_steps > MAX_STEPS) return fail(CG_EINVAL, "n_steps out of range");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
     if ((reinterpret_cast<uintptr_t>(z_in) & 7) || (reinterpret_cast<uintptr_t>(z_out) & 7))
@@ -1174,7 +1177,7 @@ CG_API cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *c
     cgk::NvtxRange nvtx_range("cg_batch_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in || !z_out || !workspace) return fail(CG_EINVAL, "NULL buffer");
-    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    if (n_steps < 0 || n_steps > MAX_STEPS) return fail(CG_EINVAL, "n_steps out of range");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
     for (size_t i = 0; i < plan->inst.size(); ++i) {
@@ -1266,7 +1269,7 @@ CG_API cg_status cg_run_host(cg_plan plan, const double *z_in_host, double *z_ou
     cgk::NvtxRange nvtx_range("cg_run_host");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (!z_in_host || !z_out_host || !workspace) return fail(CG_EINVAL, "NULL buffer");
-    if (n_steps < 0) return fail(CG_EINVAL, "n_steps < 0");
+    if (n_steps < 0 || n_steps > MAX_STEPS) return fail(CG_EINVAL, "n_steps out of range");
     const size_t nbytes = (size_t)plan->offsets.back() * sizeof(double);
     char *ws = reinterpret_cast<char *>(workspace);
     double *d_in = reinterpret_cast<double *>(ws + host_state_offset(plan));
@@ -1349,7 +1352,12 @@ int model_nj(int kmodel)
 struct TlmLayout {
     size_t jbuf_off, tan_off, total;
     int64_t tstride, tblk, jstride;
+    bool ok;               // false: the byte count does not fit (reported as CG_EINVAL)
 };
+
+// Workspace byte counts are formed in size_t; the same sum in double (exact
+// to far better than the margin) tells whether it stayed below 2^62 bytes.
+constexpr double WS_LIMIT = 4611686018427387904.0;   // 2^62
 
 // Workspace of the tangent-linear runs: header | primal scratch | stage
 // Jacobians (one stage, or n_jstages when linearized) | tangent scratch.
@@ -1364,6 +1372,9 @@ TlmLayout tlm_layout(cg_plan P, int32_t n_tan, int64_t n_jstages = 1)
     L.jbuf_off = cgk::WS_HEADER + (size_t)P->scratch_elems * sizeof(double);
     L.tan_off = L.jbuf_off + (size_t)std::max<int64_t>(1, n_jstages) * (size_t)L.jstride * sizeof(double);
     L.total = L.tan_off + (size_t)n_tan * (size_t)L.tblk * sizeof(double);
+    const double est = (double)L.jbuf_off + (double)std::max<int64_t>(1, n_jstages) * (double)L.jstride * 8.0 +
+                       (double)n_tan * (double)L.tblk * 8.0;
+    L.ok = est < WS_LIMIT;
     return L;
 }
 
@@ -1407,7 +1418,9 @@ CG_API cg_status cg_tlm_workspace_size(cg_plan plan, int32_t n_tangents, size_t 
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
     if (gate_scheme(plan->scheme))
         return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
-    *bytes = tlm_layout(plan, n_tangents).total;
+    const TlmLayout L = tlm_layout(plan, n_tangents);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
+    *bytes = L.total;
     return CG_OK;
 }
 
@@ -1419,11 +1432,13 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
     if (gate_scheme(plan->scheme))
         return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
-    if (!z0 || !zT || !workspace || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (!z0 || !zT || !workspace || n_tangents < 0 || n_steps < 0 || n_steps > MAX_STEPS)
+        return fail(CG_EINVAL, "bad argument");
     if (n_tangents > 0 && (!dz0 || !dzT)) return fail(CG_EINVAL, "NULL tangent buffer");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
     const TlmLayout L = tlm_layout(plan, n_tangents);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
     const size_t sbytes = (size_t)L.tstride * sizeof(double);
     const size_t tbytes = sbytes * (size_t)n_tangents;
     if (overlaps(z0, zT, sbytes) || (n_tangents && overlaps(dz0, dzT, tbytes)))
@@ -1465,11 +1480,14 @@ CG_API cg_status cg_tlm_run(cg_plan plan, const double *z0, const double *dz0, d
 
 CG_API cg_status cg_tlm_linearized_workspace_size(cg_plan plan, int32_t n_tangents, int64_t n_steps, size_t *bytes)
 {
-    if (!plan || !bytes || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (!plan || !bytes || n_tangents < 0 || n_steps < 0 || n_steps > MAX_STEPS)
+        return fail(CG_EINVAL, "bad argument");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
     if (gate_scheme(plan->scheme))
         return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
-    *bytes = tlm_layout(plan, n_tangents, n_steps * plan->ns).total;
+    const TlmLayout L = tlm_layout(plan, n_tangents, n_steps * plan->ns);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
+    *bytes = L.total;
     return CG_OK;
 }
 
@@ -1482,11 +1500,13 @@ static cg_status tlm_linearized(cg_plan plan, const double *z0, double *zT, cons
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "tangent-linear runs need a single-instance plan");
     if (gate_scheme(plan->scheme))
         return fail(CG_EUNSUPPORTED, "no tangent-linear model of the gate integrators");
-    if (!workspace || n_tangents < 0 || n_steps < 0) return fail(CG_EINVAL, "bad argument");
+    if (!workspace || n_tangents < 0 || n_steps < 0 || n_steps > MAX_STEPS)
+        return fail(CG_EINVAL, "bad argument");
     if (apply ? (n_tangents > 0 && (!dz0 || !dzT)) : (!z0 || !zT)) return fail(CG_EINVAL, "NULL buffer");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
     const TlmLayout L = tlm_layout(plan, n_tangents, n_steps * plan->ns);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
     const size_t sbytes = (size_t)L.tstride * sizeof(double);
     const size_t tbytes = sbytes * (size_t)n_tangents;
     if (!apply && overlaps(z0, zT, sbytes)) return fail(CG_EINVAL, "input and output partially overlap");
@@ -1577,6 +1597,7 @@ const void *lookup_adj_kernel(int kmodel, int stencil, int scheme, int cx)
 struct AdjLayout {
     int64_t c, nseg, S;
     size_t cp_off, store_off, kb_off, part_off, total;
+    bool ok;               // false: the byte count does not fit (reported as CG_EINVAL)
 };
 
 AdjLayout adj_layout(cg_plan P, int64_t n_steps, int32_t every)
@@ -1585,6 +1606,7 @@ AdjLayout adj_layout(cg_plan P, int64_t n_steps, int32_t every)
     const Inst &I = P->inst[0];
     L.S = round32((int64_t)P->nv * I.nx * I.ny);
     L.c = every > 0 ? every : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(1, n_steps))));
+    L.c = std::min<int64_t>(L.c, std::max<int64_t>(1, n_steps));   // a segment never exceeds the horizon
     L.nseg = std::max<int64_t>(1, (n_steps + L.c - 1) / L.c);
     const size_t d = sizeof(double);
     L.cp_off = cgk::WS_HEADER + (size_t)P->scratch_elems * d;
@@ -1593,6 +1615,10 @@ AdjLayout adj_layout(cg_plan P, int64_t n_steps, int32_t every)
     L.part_off = L.kb_off + (size_t)4 * L.S * d;
     const int nd = P->model == CG_FHN ? 2 : 1;
     L.total = L.part_off + (size_t)round32((int64_t)P->nblocks * (P->threads / 32) * nd) * d;
+    const double dS = (double)L.S * 8.0;
+    const double est = (double)L.cp_off + (double)L.nseg * dS + ((double)L.c * P->ns + 1.0) * dS + 4.0 * dS +
+                       8.0 * (double)round32((int64_t)P->nblocks * (P->threads / 32) * nd);
+    L.ok = est < WS_LIMIT;
     return L;
 }
 
@@ -1600,10 +1626,13 @@ AdjLayout adj_layout(cg_plan P, int64_t n_steps, int32_t every)
 
 CG_API cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, size_t *bytes)
 {
-    if (!plan || !bytes || n_steps < 0 || checkpoint_every < 0) return fail(CG_EINVAL, "bad argument");
+    if (!plan || !bytes || n_steps < 0 || n_steps > MAX_STEPS || checkpoint_every < 0)
+        return fail(CG_EINVAL, "bad argument");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
     if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
-    *bytes = adj_layout(plan, n_steps, checkpoint_every).total;
+    const AdjLayout L = adj_layout(plan, n_steps, checkpoint_every);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
+    *bytes = L.total;
     return CG_OK;
 }
 
@@ -1614,13 +1643,14 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
     if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
-    if (!z0 || !lamT || !lam0 || !workspace || n_steps < 0 || checkpoint_every < 0)
+    if (!z0 || !lamT || !lam0 || !workspace || n_steps < 0 || n_steps > MAX_STEPS || checkpoint_every < 0)
         return fail(CG_EINVAL, "bad argument");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
     cg_status st = check_plan_device(plan);
     if (st != CG_OK) return st;
     const AdjLayout L = adj_layout(plan, n_steps, checkpoint_every);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
     const Inst &I = plan->inst[0];
     const int64_t nstate = (int64_t)plan->nv * I.nx * I.ny;
     const size_t sbytes = (size_t)nstate * sizeof(double);

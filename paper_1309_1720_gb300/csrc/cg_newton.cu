@@ -127,6 +127,8 @@ static cg_status newton_sizes(cg_plan plan, int32_t restart, bool lin, int64_t p
     *tws = (*tws + 255) / 256 * 256;
     const size_t vec = ((size_t)off[1] + 31) / 32 * 32 * sizeof(double);
     *total = *tws + vec * (size_t)(restart + 4) + 4096;
+    if ((double)*tws + (double)vec * ((double)restart + 4.0) + 4096.0 >= 4611686018427387904.0)   // 2^62
+        return err(CG_EINVAL, "Newton workspace size overflows");
     return CG_OK;
 }
 
@@ -140,7 +142,7 @@ CG_API cg_status cg_newton_workspace_size(cg_plan plan, int32_t restart, size_t 
 CG_API cg_status cg_newton_linearized_workspace_size(cg_plan plan, int32_t restart, int64_t period_steps,
                                                      size_t *bytes)
 {
-    if (!plan || !bytes || restart < 1 || period_steps < 1)
+    if (!plan || !bytes || restart < 1 || period_steps < 1 || period_steps > CG_MAX_STEPS)
         return err(CG_EINVAL, "cg_newton_linearized_workspace_size: bad argument");
     size_t tws = 0;
     return newton_sizes(plan, restart, true, period_steps, &tws, bytes);
@@ -155,7 +157,8 @@ static cg_status gmres_step(cg_plan plan, const double *z0, int64_t period_steps
                             int32_t max_restarts, double rtol, double *dz, double *res_hist, int32_t *n_iter,
                             void *workspace, void *stream, bool lin)
 {
-    if (!plan || !z0 || !dz || !workspace || period_steps < 1 || restart < 1 || max_restarts < 1 || !(rtol > 0))
+    if (!plan || !z0 || !dz || !workspace || period_steps < 1 || period_steps > CG_MAX_STEPS || restart < 1 ||
+        max_restarts < 1 || !(rtol > 0))
         return err(CG_EINVAL, "cg_newton_gmres_step: bad argument");
     int64_t off[2];
     cg_status st = cg_batch_offsets(plan, off);
