@@ -122,7 +122,13 @@ def _state(t, numel, name, cuda=True):
 
 
 class Plan:
-    """An immutable stepping plan for one instance or a packed batch."""
+    """An immutable stepping plan for one instance or a packed batch.
+
+    The underlying C plan may be shared by calls on several streams, each
+    with its own workspace.  This object keeps one device workspace of its
+    own that ``run`` (without ``workspace=``), ``rhs``, ``tlm`` and
+    ``adjoint`` reuse, so calls that may overlap on different streams either
+    pass ``workspace=`` to ``run`` or use separate Plan objects."""
 
     def __init__(self, problems, tuning: Optional[dict] = None):
         L = _lib.lib()
