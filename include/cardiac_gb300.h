@@ -415,6 +415,15 @@ cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_ins
                              int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
                              int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs, int32_t *deps_out);
 
+/* Host-only preview of the schedule the adjoint's reverse stages use on a
+ * single-instance plan with mirror ghosts and grid barriers (other plans'
+ * adjoints use cg_static_schedule's): the same segments and warp split, but
+ * the n_blocks cell ranges have equal COST, a cell on the scaled boundary
+ * path (rows 0, 1, ny-2, ny-1 and the column strips starting at column <= 1
+ * or reaching column nx-2) counting 1.4.  Outputs as cg_static_schedule. */
+cg_status cg_adjoint_schedule(int32_t nx, int32_t ny, int32_t cells_x, int32_t n_blocks, int32_t warps_per_block,
+                              int32_t *segs_out, int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs);
+
 /* CG_ABI_VERSION of the loaded library. */
 int32_t cg_abi_version(void);
 

@@ -104,6 +104,9 @@ _SIGS = {
     "cg_default_params": (ctypes.c_int, [ctypes.c_int32, c_dp]),
     "cg_abi_version": (ctypes.c_int32, []),
     "cg_bounds_checked": (ctypes.c_int32, []),
+    "cg_adjoint_schedule": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     "cg_static_schedule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,

@@ -28,6 +28,10 @@ thread_local std::string g_err;
 // Longest run any entry point accepts: stage counters (n_steps x stages)
 // and per-step byte counts stay far from int64 / size_t overflow.
 constexpr int64_t MAX_STEPS = CG_MAX_STEPS;
+// Relative extra cost of a cell on the adjoint's scaled boundary path (the
+// W^-1 / W factors of mirror ghosts): about 38 FP64 instructions per cell
+// and reverse stage there against 27 in the interior.
+constexpr double ADJ_BOUNDARY_COST = 0.4;
 
 cg_status fail(cg_status st, const char *fmt, ...)
 {
@@ -139,6 +143,12 @@ struct cg_plan_s {
     std::vector<int32_t> warp_seg;
     cgk::Seg *d_segs = nullptr;
     int32_t *d_warp_seg = nullptr;
+    // the adjoint's static schedule, cost-balanced for its boundary path
+    // (single-instance mirror plans with grid barriers; else the one above)
+    std::vector<cgk::Seg> segs_adj;
+    std::vector<int32_t> warp_seg_adj;
+    cgk::Seg *d_segs_adj = nullptr;
+    int32_t *d_warp_seg_adj = nullptr;
     int32_t sched = cgk::SCHED_STATIC;
     int32_t n_tiles = 0;
     int32_t cx = 2, rows = 4, threads = 512, bpsm = 1;
@@ -436,14 +446,59 @@ bool same_config(const cg_problem &a, const cg_problem &b)
     return true;
 }
 
+// Cell ranges of the G blocks of a single nx x ny instance with equal COST
+// instead of equal cell counts: every cell the adjoint's scaled (mirror
+// boundary) path handles counts 1 + beta.  Those are the cells of rows 0, 1,
+// ny-2, ny-1 and of the column strips (32*cx wide) that start at column <= 1
+// or reach column nx-2, the same test as the adjoint kernel's per-segment
+// choice.  Returns G + 1 monotone boundaries from 0 to nx*ny.
+std::vector<int64_t> cost_balanced_ranges(int nx, int ny, int tw, int G, double beta)
+{
+    std::vector<std::pair<int, int>> bstrips;           // scaled column intervals [x0, x1)
+    int64_t E = 0;                                       // scaled cells of an interior row
+    for (int x0 = 0; x0 < nx; x0 += tw)
+        if (x0 <= 1 || x0 + tw >= nx - 1) {
+            bstrips.emplace_back(x0, std::min(nx, x0 + tw));
+            E += std::min(nx, x0 + tw) - x0;
+        }
+    auto scaled_cols = [&](int64_t r) {                  // scaled cells among columns [0, r)
+        int64_t t = 0;
+        for (const auto &iv : bstrips) t += std::max<int64_t>(0, std::min<int64_t>(r, iv.second) - iv.first);
+        return t;
+    };
+    auto in_rows = [&](int64_t y) { return y <= 1 || y >= ny - 2; };
+    auto cost = [&](int64_t c) {                         // cost of cells [0, c)
+        const int64_t y = c / nx, r = c % nx;
+        const int64_t nr = std::min<int64_t>(y, 2) + std::max<int64_t>(0, y - std::max(2, ny - 2));
+        const int64_t B = nr * nx + (y - nr) * E + (r == 0 ? 0 : (in_rows(y) ? r : scaled_cols(r)));
+        return (double)c + beta * (double)B;
+    };
+    const int64_t N = (int64_t)nx * ny;
+    const double total = cost(N);
+    std::vector<int64_t> cb(G + 1, 0);
+    cb[G] = N;
+    for (int b = 1; b < G; ++b) {
+        const double target = total * b / G;
+        int64_t lo = cb[b - 1], hi = N;                  // smallest c with cost(c) >= target
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (cost(mid) >= target) hi = mid; else lo = mid + 1;
+        }
+        cb[b] = lo;
+    }
+    return cb;
+}
+
 // Static schedule: the cells of all instances (in plan order, row-major
 // inside an instance) are cut into G equal ranges, one per block; a block's
 // range becomes column strips of 32*cx cells by row ranges, and those are
 // cut into NW pieces with equal numbers of strip-rows, one per warp.  Every
 // SM therefore gets the same FP64 work per stage, and so does each of its
-// warps (to within one row).
+// warps (to within one row).  With ranges given (cost_balanced_ranges), the
+// blocks take those instead of equal cell counts.
 void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int cx, int G, int NW,
-                     std::vector<cgk::Seg> &segs, std::vector<int32_t> &warp_seg)
+                     std::vector<cgk::Seg> &segs, std::vector<int32_t> &warp_seg,
+                     const std::vector<int64_t> *ranges = nullptr)
 {
     const int n = (int)nxs.size();
     std::vector<int64_t> cstart(n + 1, 0);
@@ -454,7 +509,7 @@ void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t>
     warp_seg.assign((size_t)G * NW + 1, 0);
     int k0 = 0;
     for (int b = 0; b < G; ++b) {
-        const int64_t c0 = N * b / G, c1 = N * (b + 1) / G;
+        const int64_t c0 = ranges ? (*ranges)[b] : N * b / G, c1 = ranges ? (*ranges)[b + 1] : N * (b + 1) / G;
         std::vector<cgk::Seg> bs;
         while (k0 < n && cstart[k0 + 1] <= c0) ++k0;
         for (int k = k0; k < n && cstart[k] < c1; ++k) {
@@ -814,6 +869,12 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
                         P->bc != CG_BC_PERIODIC &&
                         (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
+        if (P->inst.size() == 1 && P->bc == CG_BC_MIRROR && !gate_scheme(P->scheme) &&
+            P->sync_mode == cgk::SYNC_GRID) {
+            const std::vector<int64_t> cb =
+                cost_balanced_ranges(nxs[0], nys[0], 32 * P->cx, P->nblocks, ADJ_BOUNDARY_COST);
+            static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs_adj, P->warp_seg_adj, &cb);
+        }
     }
     if (e == cudaSuccess && P->tb_k > 0) {
         const cg_status st = tb_setup(P);
@@ -842,10 +903,22 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_warp_seg, P->warp_seg.data(), sizeof(int32_t) * P->warp_seg.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !P->warp_seg_adj.empty()) {
+        e = cudaMalloc(&P->d_segs_adj, sizeof(cgk::Seg) * std::max<size_t>(1, P->segs_adj.size()));
+        if (e == cudaSuccess && !P->segs_adj.empty())
+            e = cudaMemcpy(P->d_segs_adj, P->segs_adj.data(), sizeof(cgk::Seg) * P->segs_adj.size(),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&P->d_warp_seg_adj, sizeof(int32_t) * P->warp_seg_adj.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_warp_seg_adj, P->warp_seg_adj.data(), sizeof(int32_t) * P->warp_seg_adj.size(),
+                           cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         if (P->d_inst) cudaFree(P->d_inst);
         if (P->d_segs) cudaFree(P->d_segs);
         if (P->d_warp_seg) cudaFree(P->d_warp_seg);
+        if (P->d_segs_adj) cudaFree(P->d_segs_adj);
+        if (P->d_warp_seg_adj) cudaFree(P->d_warp_seg_adj);
         if (P->d_deps) cudaFree(P->d_deps);
         if (P->d_tab) cudaFree(P->d_tab);
         delete P;
@@ -966,6 +1039,8 @@ CG_API cg_status cg_plan_destroy(cg_plan plan)
     if (plan->d_inst) cudaFree(plan->d_inst);
     if (plan->d_segs) cudaFree(plan->d_segs);
     if (plan->d_warp_seg) cudaFree(plan->d_warp_seg);
+    if (plan->d_segs_adj) cudaFree(plan->d_segs_adj);
+    if (plan->d_warp_seg_adj) cudaFree(plan->d_warp_seg_adj);
     if (plan->d_deps) cudaFree(plan->d_deps);
     if (plan->d_tab) cudaFree(plan->d_tab);
     delete plan;
@@ -1710,6 +1785,10 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
         st = launch_stages(plan, plan->kernel, fargs, a, 0, m * plan->ns, plan->nblocks, s);
         if (st != CG_OK) return st;
         base_args(plan, a, cp + j * L.S, nullptr, ws);
+        if (plan->d_warp_seg_adj) {
+            a.segs = plan->d_segs_adj;
+            a.warp_seg = plan->d_warp_seg_adj;
+        }
         cgk::AdjArgs b;
         b.store = store;
         b.kb0 = kb;
@@ -1765,9 +1844,11 @@ CG_API cg_status cg_default_params(int32_t model, double *out)
     return CG_OK;
 }
 
-CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
-                                    int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
-                                    int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs, int32_t *deps_out)
+namespace {
+
+cg_status schedule_preview(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x, int32_t n_blocks,
+                           int32_t warps_per_block, int32_t *segs_out, int64_t segs_cap, int32_t *warp_seg_out,
+                           int64_t *n_segs, int32_t *deps_out, bool adjoint)
 {
     if (!nx || !ny || n_inst < 1 || (cells_x != 1 && cells_x != 2) || n_blocks < 1 || warps_per_block < 1 ||
         !warp_seg_out || !n_segs)
@@ -1777,7 +1858,12 @@ CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_
         if (nxs[i] < 1 || nys[i] < 1) return fail(CG_EINVAL, "instance %d has an empty grid", i);
     std::vector<cgk::Seg> segs;
     std::vector<int32_t> ws;
-    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws);
+    std::vector<int64_t> cb;
+    if (adjoint) {
+        if (n_inst != 1) return fail(CG_EINVAL, "the adjoint schedule is for one instance");
+        cb = cost_balanced_ranges(nxs[0], nys[0], 32 * cells_x, n_blocks, ADJ_BOUNDARY_COST);
+    }
+    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws, adjoint ? &cb : nullptr);
     *n_segs = (int64_t)segs.size();
     std::copy(ws.begin(), ws.end(), warp_seg_out);
     if (deps_out) {
@@ -1794,6 +1880,24 @@ CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_
         std::memcpy(segs_out, segs.data(), sizeof(cgk::Seg) * segs.size());
     }
     return CG_OK;
+}
+
+}  // namespace
+
+CG_API cg_status cg_static_schedule(const int32_t *nx, const int32_t *ny, int32_t n_inst, int32_t cells_x,
+                                    int32_t n_blocks, int32_t warps_per_block, int32_t *segs_out,
+                                    int64_t segs_cap, int32_t *warp_seg_out, int64_t *n_segs, int32_t *deps_out)
+{
+    return schedule_preview(nx, ny, n_inst, cells_x, n_blocks, warps_per_block, segs_out, segs_cap, warp_seg_out,
+                            n_segs, deps_out, false);
+}
+
+CG_API cg_status cg_adjoint_schedule(int32_t nx, int32_t ny, int32_t cells_x, int32_t n_blocks,
+                                     int32_t warps_per_block, int32_t *segs_out, int64_t segs_cap,
+                                     int32_t *warp_seg_out, int64_t *n_segs)
+{
+    return schedule_preview(&nx, &ny, 1, cells_x, n_blocks, warps_per_block, segs_out, segs_cap, warp_seg_out,
+                            n_segs, nullptr, true);
 }
 
 CG_API int32_t cg_abi_version(void)

@@ -152,12 +152,11 @@ def test_adjoint_and_tlm_other_sync_modes(cuda_ok, flags):
     a1, d1 = Plan(p).adjoint(z0, lamT, 21, checkpoint_every=4)
     _, t1 = Plan(p).tlm(z0, dz, 21)
     assert torch.equal(a0, a1) and torch.equal(t0, t1)
-    if flags == 1 << 1:
-        # one launch per stage adds each stage's warp sums to the dL/dD slots
-        # instead of each launch's, a different association of the same terms
-        assert torch.allclose(d0, d1, rtol=1e-10, atol=0)
-    else:
-        assert torch.equal(d0, d1)
+    # dL/dD: one launch per stage adds each stage's warp sums to the dL/dD
+    # slots instead of each launch's, and neighbour synchronisation keeps the
+    # equal-cell schedule (the grid-barrier adjoint balances its boundary
+    # cost), so the same terms are associated differently
+    assert torch.allclose(d0, d1, rtol=1e-10, atol=0)
 
 
 def test_dLdD_bitwise_reproducible(cuda_ok):

@@ -84,3 +84,64 @@ def test_exact_cover_and_balance(L, nxs, nys, cx, G, NW):
                 lo[dst] = np.minimum(lo[dst], src)
                 hi[dst] = np.maximum(hi[dst], src)
         assert np.all(deps[o, 0] <= lo) and np.all(hi <= deps[o, 1])
+
+
+def adjoint_schedule(L, nx, ny, cx, G, NW):
+    ws = (ctypes.c_int32 * (G * NW + 1))()
+    ns = ctypes.c_int64()
+    assert L.cg_adjoint_schedule(nx, ny, cx, G, NW, None, 0, ws, ctypes.byref(ns)) == 0
+    segs = (ctypes.c_int32 * (10 * max(1, ns.value)))()
+    assert L.cg_adjoint_schedule(nx, ny, cx, G, NW, segs, ns.value, ws, ctypes.byref(ns)) == 0
+    return np.array(segs[:10 * ns.value]).reshape(-1, 10), np.array(ws[:])
+
+
+def _scaled(nx, ny, tw):
+    """Cells on the adjoint's scaled boundary path: rows 0, 1, ny-2, ny-1 and
+    the column strips starting at column <= 1 or reaching column nx-2."""
+    m = np.zeros((ny, nx), dtype=bool)
+    m[:2] = True
+    m[max(0, ny - 2):] = True
+    for x0 in range(0, nx, tw):
+        if x0 <= 1 or x0 + tw >= nx - 1:
+            m[:, x0:x0 + tw] = True
+    return m
+
+
+@pytest.mark.parametrize("nx,ny,cx,G,NW", [
+    (512, 512, 2, 152, 16), (1024, 1024, 2, 152, 16), (129, 65, 2, 152, 16), (67, 45, 1, 7, 4),
+    (2, 2, 1, 152, 16), (3, 7, 2, 5, 4), (4096, 3, 2, 152, 16), (65, 300, 1, 13, 8),
+])
+def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
+    """Exact cover by warp segments, warps inside a block within one
+    strip-row of each other, and block costs (1.4 per scaled cell, 1
+    otherwise) equal to within one cell at each end of a block (2 x 1.4)."""
+    segs, ws = adjoint_schedule(L, nx, ny, cx, G, NW)
+    tw = 32 * cx
+    own = np.full((ny, nx), -1, dtype=np.int64)
+    per_warp = np.zeros(G * NW, dtype=np.int64)
+    for w in range(G * NW):
+        for k in range(ws[w], ws[w + 1]):
+            inst, x0, y0, y1, ra, a0, a1, rb, b0, b1 = segs[k]
+            assert inst == 0 and x0 % tw == 0 and 0 <= y0 <= y1 < ny
+            per_warp[w] += y1 - y0 + 1
+            x1 = min(x0 + tw, nx)
+            blk = np.ones((y1 - y0 + 1, x1 - x0), dtype=bool)
+            xs = np.arange(x0, x1)
+            if y0 <= ra <= y1:
+                blk[ra - y0] = (xs >= a0) & (xs < a1)
+            if y0 <= rb <= y1:
+                blk[rb - y0] = (xs >= b0) & (xs < b1)
+            sub = own[y0:y1 + 1, x0:x1]
+            assert np.all(sub[blk] == -1)
+            sub[blk] = w // NW
+    assert np.all(own >= 0)
+    for b in range(G):
+        pw = per_warp[b * NW:(b + 1) * NW]
+        assert pw.max() - pw.min() <= 1
+    # blocks own consecutive row-major ranges, in block order
+    flat = own.reshape(-1)
+    assert np.all(np.diff(flat) >= 0)
+    cost = np.where(_scaled(nx, ny, tw), 1.4, 1.0).reshape(-1)
+    per_block = np.array([cost[flat == b].sum() for b in range(G)])
+    if nx * ny >= 4 * G:
+        assert per_block.max() - per_block.min() <= 2.8 + 1e-9
