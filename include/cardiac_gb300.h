@@ -228,7 +228,11 @@ cg_status cg_batch_run(cg_plan plan, const double *const *z_in, double *const *z
  * clears its status and synchronisation words itself), so calls that
  * overlap on the GPU race: issue them on one stream or otherwise serialise
  * them.  status_dev (device, may be NULL) receives the call's CG_DEV_* bits
- * once the run has finished on the stream. */
+ * once the run has finished on the stream.  Because every call's status
+ * word lives in the shared array, cg_get_device_status on a plan whose
+ * latest run went through this call reports the status of whichever
+ * cg_run_noalloc call ran last on that device; use status_dev for the
+ * status of one particular call. */
 cg_status cg_run_noalloc(cg_plan plan, const double *z_in, double *z_out, int64_t n_steps,
                          uint32_t *status_dev, void *stream);
 

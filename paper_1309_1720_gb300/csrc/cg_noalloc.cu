@@ -6,6 +6,7 @@
 // start-up.  They build the plan at set-up time and step with this call,
 // which takes its scratch from a fixed, statically allocated device array
 // instead of a caller-provided workspace.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
@@ -26,7 +27,9 @@ static __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
 // Device address of g_scratch per device, looked up once per device.  In
 // host code the name g_scratch is only a host-side stand-in, so the address
 // must come from cudaGetSymbolAddress, called with that device current.
-void *g_scratch_ptr[MAX_DEVICES] = {};
+// Atomic entries: host threads making their first call on a device at the
+// same time may both look the address up; each stores the same value.
+std::atomic<void *> g_scratch_ptr[MAX_DEVICES] = {};
 
 }  // namespace
 
@@ -46,14 +49,13 @@ CG_API cg_status cg_run_noalloc(cg_plan plan, const double *z_in, double *z_out,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return cgk::set_last_error(CG_ECUDA, "cg_run_noalloc: no usable current device");
-    if (g_scratch_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || p == nullptr)
+    void *ws = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (ws == nullptr) {
+        const cudaError_t e = cudaGetSymbolAddress(&ws, g_scratch);
+        if (e != cudaSuccess || ws == nullptr)
             return cgk::set_last_error(CG_ECUDA, "cg_run_noalloc: cudaGetSymbolAddress of the static scratch failed");
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(ws, std::memory_order_release);
     }
-    void *ws = g_scratch_ptr[dev];
     st = cg_run(plan, z_in, z_out, n_steps, ws, stream);
     if (st != CG_OK || status_dev == nullptr) return st;
     const cudaError_t e = cudaMemcpyAsync(status_dev, ws, sizeof(uint32_t), cudaMemcpyDeviceToDevice,

@@ -36,6 +36,9 @@ def test_noalloc_matches_cg_run_twice(cuda_ok):
         assert _noalloc(plan, z0, out, steps, status) == 0
         torch.cuda.synchronize()
         assert int(status.item()) == 0, call
+        # the same kernel on the same inputs: equal bit for bit (so within
+        # the 1e-12 parity tolerance as well)
+        assert torch.equal(out, ref), call
         assert field_rel_err(out.cpu().numpy(), ref.cpu().numpy()) <= TOL, call
 
 
