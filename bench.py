@@ -1,14 +1,17 @@
 #!/usr/bin/env python3
 """Benchmark of the fused FP64 cardiac stepper on GB300.
 
-Workload (one bench step): the two-field FitzHugh-Nagumo model of Sect. 2 on
-a 1024 x 1024 grid (dx = 0.04), 9-point isotropic Laplacian (alpha_d = 1/6),
-no-flux mirror ghosts, classic RK4 with dt = 4e-4, 10000 time steps from the
-seeded broken-wave state; one persistent kernel launch per bench step.
+Workload (one bench step): the paper's four-field Bueno-Orovio-Cherry-Fenton
+model (Sect. 2, Eq. bochfe; voltage u and gates v, w, s) on a 2048 x 2048
+grid (dx = 0.03 cm), anisotropic diagonal diffusion Dxx = 1.171e-3 cm^2/ms =
+4 Dyy on the 9-point stencil (alpha_d = 1/6), no-flux mirror ghosts, classic
+RK4 with dt = 0.05 ms, 5000 time steps from the seeded eight-core spiral
+state; one persistent kernel launch per bench step.
 Metric: FP64 giga cell-updates per second (GCUPS) and the fraction of the
-FP64-pipe roofline.  Also reported: the same metric end to end through the
-public API with host buffers, the other workloads (small grid, four-field
-model), and the CPU oracle on a bounded sample of the workload.
+FP64 roofline.  Also reported: the same metric end to end through the public
+API with host buffers, the other workloads (the 1024^2 two-field RK4 run,
+the small grid, the gate integrators, Karma, the batch, the tangent-linear
+and adjoint runs), and the CPU oracle on a bounded sample of the workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -29,20 +32,49 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FP64 GCUPS & % of HBM/FP64 roofline; batched and adjoint/JVP vs plain stepper"
-NX = NY = 1024
-STEPS_PER_RUN = 10000
-DT = 4e-4
-# Algorithmic FP64 flops per cell-update, FMA = 2 (per RK stage: 9-point
-# Laplacian 2 x 11, local terms 8, D scaling 2 x 2, combine 2 x 4; x 4 stages).
-FLOPS_PER_CELL_UPDATE = 168
-# Algorithmic HBM bytes per cell-update of a fused step: each field read and
-# written once (2 fields x 8 B x 2).
-BYTES_PER_CELL_UPDATE = 32
+
+# ---------------------------------------------------------------- workload
+NX = NY = 2048
+DX = 0.03                      # cm (Sect. 2)
+D_XX = 1.171e-3                # cm^2/ms (Sect. 2: D = 1.171 cm^2/s)
+D_YY = D_XX / 4.0
+DT = 0.05                      # ms
+STEPS_PER_RUN = 5000
+# Algorithmic HBM bytes per cell-update of a fused step: four fields read
+# and written once (4 x 8 B x 2).
+BYTES_PER_CELL_UPDATE = 64
+
+# Algorithmic FP64 flops of one cell and one RK stage (FMA = 2, add = 1,
+# multiply = 1), per branch of the local terms, including the anisotropic
+# 9-point stencil on u (row-sum form) and the stage combine of the four
+# fields.  A branch is the switch state of the cell's own voltage:
+#   rest     u <= theta_w - 1/(2k): the v and w switches H_k are exactly 0,
+#            so every term they multiply is exactly 0 and is not evaluated;
+#   excited  u >= theta_v + 1/(2k): every switch is exactly 1;
+#   general  in between: the whole of Eq. (bochfe).
+# The sigmoid, exponential and reciprocal count at the flops of the
+# library's own evaluations (Tang's table-driven exponential, a cubic
+# Newton reciprocal), which take the place of the tanh and division costs
+# T and R.  Frozen from ncu's per-opcode counters (DFMA x 2 + DADD + DMUL
+# thread instructions per cell and stage) on uniform states where every
+# warp takes one branch, in the workload's tuned launch shape:
+#   rest     DFMA 48.5, DADD 14.5, DMUL 13.0 -> 124.5
+#   excited  DFMA 34.5, DADD 13.5, DMUL 13.0 ->  95.5
+#   general  DFMA 71.5, DADD 23.5, DMUL 31.0 -> 197.5
+# A cell is charged its own branch, so a warp whose lanes straddle a switch
+# (it runs the general path for all 32) does more than this count.
+BOCF_STAGE_FLOPS = {"rest": 124.5, "excited": 95.5, "general": 197.5}
 # DRAM bytes per cell-update measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on a 20-step launch of this workload; traffic grows
-# in proportion to the steps of a launch (L2 write-backs of the resident
-# working set), so one bench launch moves this times its cell-updates.
-MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 37.3
+# dram__bytes_write.sum) on a 2-step launch of this workload in its tuned
+# shape: every RK stage streams the state, the accumulator and the stage
+# buffers of the four fields (640 MB, more than L2) through HBM, so the
+# traffic grows in proportion to the steps of a launch.
+MEASURED_DRAM_BYTES_PER_CELL_UPDATE = 508.8
+
+# the 1024^2 two-field row (the FitzHugh-Nagumo model, 9-point isotropic,
+# RK4): per stage 9-point Laplacian 2 x 11, local terms 8, D scaling 2 x 2,
+# combine 2 x 4; x 4 stages
+FHN_FLOPS_PER_CELL_UPDATE = 168
 
 
 def parse():
@@ -53,14 +85,15 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--profile-case", nargs="?", const="fhn", default=None,
-                    choices=["fhn", "bocf", "karma", "tlm", "adj", "c1"],
-                    help="run a short case twice and exit (for ncu captures): 20 steps of the "
-                         "1024^2 workload (fhn), 2 steps of the 2048^2 four-field model (bocf), 10 steps "
-                         "of the 2048^2 Karma model (karma), or on "
-                         "the 512^2 two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of "
-                         "16 steps (adj), or 200 steps of the 128^2 Euler problem with 4 steps per grid "
-                         "barrier (c1)")
+    ap.add_argument("--profile-case", nargs="?", const="bocf", default=None,
+                    choices=["fhn", "bocf", "bocf-branches", "fp64-probe", "karma", "tlm", "adj", "c1"],
+                    help="run a short case and exit (for ncu captures): 2 steps of the 2048^2 four-field "
+                         "workload in its tuned launch shape (bocf); 2 steps of the same plan on three "
+                         "uniform states, one per branch of the local terms (bocf-branches); the FP64 "
+                         "DFMA, DADD and DMUL rate probes (fp64-probe); 20 steps of the 1024^2 two-field "
+                         "RK4 workload (fhn); 10 steps of the 2048^2 Karma model (karma); on the 512^2 "
+                         "two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of 16 steps "
+                         "(adj); or 200 steps of the 128^2 Euler problem with 4 steps per grid barrier (c1)")
     ap.add_argument("--experiment", default=None,
                     choices=["all", "timing", "grid", "convergence", "orbit", "snapshots"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
@@ -91,6 +124,34 @@ def replica_throughput(cell_updates_per_rank: float, ws: int, seconds: float) ->
     path runs one instance per GPU; replicas share nothing), so the job's
     cell-updates are ws times one rank's, over the slowest rank's time."""
     return ws * cell_updates_per_rank / seconds / 1e9
+
+
+def bocf_flops_per_cell_update(mix) -> float:
+    """Algorithmic FP64 flops of one RK4 cell-update of the four-field model
+    for a branch mix {branch: fraction of cell-stages}."""
+    return 4.0 * sum(BOCF_STAGE_FLOPS[b] * f for b, f in mix.items())
+
+
+def bocf_branch_bounds(params):
+    """Voltage bounds of the rest and excited branches: u <= theta_w - 1/(2k)
+    puts the v and w switches at exactly 0, u >= max(thresholds) + 1/(2k)
+    puts all four at exactly 1 (params in cg_default_params order)."""
+    th_v, th_w, th_vm, th_o, k = params[2], params[3], params[4], params[5], params[28]
+    return min(th_v, th_w) - 0.5 / k, max(th_v, th_w, th_vm, th_o) + 0.5 / k
+
+
+def headline_problem(api):
+    return api.Problem(model=api.BOCF, nx=NX, ny=NY, dx=DX, D=(D_XX,), Dyy=(D_YY,), stencil=api.STENCIL9,
+                       alpha_d=1 / 6, scheme=api.RK4, dt=DT)
+
+
+def headline_state(I):
+    return I.bocf_spiral_cores(NX, NY, seed=0)
+
+
+def oracle_headline_problem(O):
+    return O.problem(O.BOCF, nx=NX, ny=NY, dx=DX, Dxx=[D_XX, 0, 0, 0], Dyy=[D_YY, 0, 0, 0], stencil=O.ST9,
+                     alpha_d=1 / 6, scheme=O.RK4, dt=DT)
 
 
 class ClockSampler:
@@ -153,7 +214,8 @@ class ClockSampler:
 
 
 def measure_fp64_peak():
-    """FP64 DFMA throughput of this GPU (TFLOP/s) from the library's probe."""
+    """FP64 DFMA throughput of this GPU (TFLOP/s, FMA = 2) from the library's
+    probe, best of three."""
     import ctypes
     from paper_1309_1720_gb300 import _lib
     L = _lib.lib()
@@ -167,28 +229,28 @@ def measure_fp64_peak():
 
 def cpu_baseline(seconds_target=12.0):
     """The oracle as it stands (single thread) on a bounded sample of the
-    workload: the same 1024^2 RK4 9-point problem for a few steps."""
+    workload: the same 2048^2 four-field RK4 problem for a few steps."""
     import oracle as O
     from paper_1309_1720_gb300 import inputs as I
-    z = I.fhn_broken_wave(NX, NY, seed=0)
-    p = O.problem(O.FHN, nx=NX, ny=NY, dx=0.04, stencil=O.ST9, alpha_d=1 / 6, scheme=O.RK4, dt=DT)
+    z = headline_state(I)
+    p = oracle_headline_problem(O)
     t = time.perf_counter()
-    z1 = O.step(p, z, 2)
-    per = (time.perf_counter() - t) / 2
-    n = int(max(3, min(200, seconds_target / max(per, 1e-6))))
+    z1 = O.step(p, z, 1)
+    per = time.perf_counter() - t
+    n = int(max(2, min(50, seconds_target / max(per, 1e-6))))
     t = time.perf_counter()
     O.step(p, z1, n)
     dt = time.perf_counter() - t
     out = {"value": NX * NY * n / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-           "sample": "%d RK4 steps of the 1024x1024 9-point two-field workload, single-threaded C oracle "
-                     "(-O2 -ffp-contract=off), rate extrapolated to the full run" % n,
+           "sample": "%d RK4 steps of the 2048x2048 four-field anisotropic 9-point workload, single-threaded C "
+                     "oracle (-O2 -ffp-contract=off), rate extrapolated to the full run" % n,
            "seconds": dt}
     # every host core: one independent single-threaded copy of the same
     # oracle per core on the same sample (ctypes releases the GIL during the
     # call, so the copies run in parallel; the oracle itself is unchanged)
     import threading
     cores = os.cpu_count() or 1
-    m = max(2, n // 4)
+    m = 2
     copies = [z1.copy() for _ in range(cores)]
     threads = [threading.Thread(target=O.step, args=(p, c, m)) for c in copies]
     t = time.perf_counter()
@@ -204,20 +266,23 @@ def cpu_baseline(seconds_target=12.0):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, single-threaded, on the headline
+    workload; each bench step is a bounded sample of one RK4 time step of
+    the 2048^2 four-field problem (the rate is per cell-update)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle as O
     from paper_1309_1720_gb300 import inputs as I
-    z = I.fhn_broken_wave(NX, NY, seed=0)
-    p = O.problem(O.FHN, nx=NX, ny=NY, dx=0.04, stencil=O.ST9, alpha_d=1 / 6, scheme=O.RK4, dt=DT)
-    sample_steps = 10
+    z = headline_state(I)
+    p = oracle_headline_problem(O)
+    sample_steps = 1
     for _ in range(args.warmup):
-        O.step(p, z, 1)
+        z = O.step(p, z, sample_steps)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        O.step(p, z, sample_steps)
+        z = O.step(p, z, sample_steps)
         times.append(time.perf_counter() - t)
     tot = sum(times)
     val = NX * NY * sample_steps * args.steps / tot / 1e9
@@ -227,24 +292,26 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": workload_config(),
         "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-                         "sample": "each step: %d RK4 time steps of the 1024x1024 9-point two-field workload "
-                                   "on the single-threaded C oracle" % sample_steps},
+                         "sample": "each step: %d RK4 time step of the 2048x2048 four-field anisotropic 9-point "
+                                   "workload on the single-threaded C oracle" % sample_steps},
         "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def workload_config():
-    return {"workload": "fhn-1024x1024-9pt-rk4-10000steps",
-            "model": "FitzHugh-Nagumo (eps, a1, a0) = (0.05, 1.5, -0.1), D = (1, 1.5)",
-            "grid": [NX, NY], "dx": 0.04, "stencil": "9-point isotropic, alpha_d = 1/6",
-            "bc": "no-flux mirror", "scheme": "RK4", "dt": DT, "time_steps_per_bench_step": STEPS_PER_RUN,
-            "ic": "seeded broken wave (seed 0)",
-            "l2": "flushed (256 MB write) between timed bench steps; the 80 MB working set is L2-resident "
-                  "within a run by design"}
+    return {"workload": "bocf-2048x2048-aniso9pt-rk4-5000steps",
+            "model": "Bueno-Orovio-Cherry-Fenton four-field model (Eq. bochfe), epicardial constants, H_k with "
+                     "k = 28.4",
+            "grid": [NX, NY], "dx_cm": DX, "D_cm2_per_ms": {"xx": D_XX, "yy": D_YY},
+            "stencil": "9-point anisotropic diagonal tensor, alpha_d = 1/6", "bc": "no-flux mirror",
+            "scheme": "RK4", "dt_ms": DT, "time_steps_per_bench_step": STEPS_PER_RUN,
+            "ic": "seeded eight-core spiral state (seed 0) plus 1e-3 noise",
+            "l2": "inputs larger than L2: the 128 MiB state and 512 MiB of stage buffers are streamed from HBM "
+                  "each stage; L2 also flushed (256 MB write) between timed bench steps"}
 
 
-def secondary_rows(torch, plan_cls, I, api, peak_tflops):
+def secondary_rows(torch, plan_cls, I, api, peak_tflops, head_tuning):
     """Short rate measurements of the other workloads (rate-based; truncated
     step counts are stated)."""
     rows = {}
@@ -275,20 +342,44 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
     rows["fhn-128x128-5pt-euler-1000steps"] = {"gcups": 128 * 128 * 1000 / t / 1e9, "seconds": t, "tuning": tun}
     plan.close()
 
-    # 2048^2 four-field model, anisotropic 9-point, RK4 (500 of the 5000 steps)
-    n, steps = 2048, 500
-    p = api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
-                    stencil=api.STENCIL9, scheme=api.RK4, dt=0.05)
-    z = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
-    tun = autotune.tune([p], z, n_steps=10)
-    plan = autotune.tuned_plan([p], z, n_steps=10)
-    t = timed(plan, z, steps, reps=2)
-    rows["bocf-2048x2048-aniso9pt-rk4"] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "tuning": tun,
-                                           "steps_timed": steps, "note": "rate of 500 of the 5000 steps"}
+    # the 1024^2 two-field workload: FitzHugh-Nagumo, 9-point isotropic,
+    # RK4, dt = 4e-4, 10000 steps from the seeded broken wave (whole runs,
+    # L2 flushed between them; the 80 MB working set is L2-resident within a
+    # run by design)
+    n, steps = 1024, 10000
+    p2 = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, stencil=api.STENCIL9, alpha_d=1 / 6, scheme=api.RK4,
+                     dt=4e-4)
+    z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
+    tun2 = autotune.tune([p2], z, n_steps=200)
+    plan = autotune.tuned_plan([p2], z, n_steps=200)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(z)
+    plan.run(z, steps, out=out)
+    ts = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.run(z, steps, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    plan.status()
+    t = statistics.median(ts)
+    ach = FHN_FLOPS_PER_CELL_UPDATE * n * n * steps / t / 1e12
+    rows["fhn-1024x1024-9pt-rk4-10000steps"] = {
+        "gcups": n * n * steps / t / 1e9, "seconds": t, "tuning": tun2,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": ach / peak_tflops, "flops_per_cell_update": FHN_FLOPS_PER_CELL_UPDATE},
+        "note": "median of 3 whole runs, L2 flushed between them"}
     plan.close()
-    # the same workload with the tanh terms as smoothed steps (Sect. 6 variant;
-    # a different model), and with the gate integrators of Table 2 (one stage
-    # per step: explicit Euler in u, Rush-Larsen / implicit Euler in v, w, s)
+    del flush, out, z
+
+    # the gate integrators and the tanh variant on the headline workload
+    n, steps = NX, 500
+    p = headline_problem(api)
+    z = torch.from_numpy(headline_state(I)).cuda()
+    tun = head_tuning
     for name, kw in [("bocf-2048x2048-aniso9pt-rk4-tanh-as-hk", dict(flags=api.FLAG_TANH_AS_HK)),
                      ("bocf-2048x2048-aniso9pt-rush-larsen", dict(scheme=api.RUSH_LARSEN)),
                      ("bocf-2048x2048-aniso9pt-implicit-euler", dict(scheme=api.IMPLICIT_EULER))]:
@@ -297,7 +388,7 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops):
         plan = autotune.plan_for([q], tun)
         t = timed(plan, z, steps, reps=2)
         rows[name] = {"gcups": n * n * steps / t / 1e9, "seconds": t, "steps_timed": steps,
-                      "note": "launch shape of the RK4 row"}
+                      "note": "rate of 500 steps, launch shape of the headline RK4 workload"}
         plan.close()
 
     # the Karma model (Eq. karma): the 256^2 grid of the paper's timing
@@ -703,6 +794,87 @@ def paper_experiments(which):
                           "T": {k: m["T"] for k, m in models.items()}, "results": conv}), flush=True)
 
 
+def profile_case(args):
+    """Short runs for ncu captures (run twice where a launch is captured
+    after a warm one)."""
+    import ctypes
+    import torch
+    from paper_1309_1720_gb300 import Plan, _lib, api, autotune, inputs as I
+    case = args.profile_case
+    if case == "fp64-probe":
+        # the DFMA, DADD and DMUL rate probes at their default size (two
+        # launches each: a warm-up half as long, then the timed one)
+        L = _lib.lib()
+        rate = ctypes.c_double()
+        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+            _lib.check(L.cg_measure_fp64_rate(op, 0, ctypes.byref(rate), None))
+            print("%s %.4e per s" % (name, rate.value))
+        print("profile case done")
+        return
+    if case == "c1":
+        cp = api.Problem(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
+        plan = Plan(cp, tuning=dict(schedule=2, rows=4, threads=512))
+        z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
+        for _ in range(2):
+            plan.run(z, 200)
+        plan.status()
+    elif case in ("tlm", "adj"):
+        n = 512
+        gp = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, scheme=api.RK4, dt=2.5e-4)
+        plan = Plan(gp)
+        z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
+        for _ in range(2):
+            if case == "tlm":
+                dz0 = torch.from_numpy(np.stack([I.unit_direction(z.shape, 2, offset=i * z.numel())
+                                                 for i in range(64)])).cuda()
+                plan.tlm(z, dz0, 4)
+            else:
+                plan.adjoint(z, z.clone(), 16)
+        plan.status()
+    elif case == "fhn":
+        # 1024^2 two-field 9-point RK4, 20 steps, its tuned launch shape
+        n = 1024
+        fp = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, stencil=api.STENCIL9, alpha_d=1 / 6,
+                         scheme=api.RK4, dt=4e-4)
+        z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
+        plan = autotune.plan_for([fp], autotune.tune([fp], z, n_steps=200))
+        out = torch.empty_like(z)
+        for _ in range(2):
+            plan.run(z, 20, out=out)
+        plan.status()
+    elif case == "karma":
+        n = 2048
+        kp = api.Problem(model=api.KARMA, nx=n, ny=n, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,), scheme=api.RK4,
+                         dt=0.05)
+        z = torch.from_numpy(I.karma_broken_wave(n, n, seed=0)).cuda()
+        plan = autotune.plan_for([kp], autotune.tune([kp], z, n_steps=10))
+        out = torch.empty_like(z)
+        for _ in range(2):
+            plan.run(z, 10, out=out)
+        plan.status()
+    else:
+        # the headline workload's plan in its tuned launch shape
+        bp = headline_problem(api)
+        z = torch.from_numpy(headline_state(I)).cuda()
+        plan = autotune.plan_for([bp], autotune.tune([bp], z, n_steps=10))
+        out = torch.empty_like(z)
+        if case == "bocf":
+            for _ in range(2):
+                plan.run(z, 2, out=out)
+        else:
+            # one launch per branch of the local terms: uniform states whose
+            # voltage puts every cell (so every warp) on that branch (rest:
+            # u = 0; excited: u = 1; general: u = 0.2, between the w and v
+            # switches), 2 steps each
+            for u, v, w, s in ((0.0, 0.9, 0.8, 0.1), (1.0, 0.0, 0.5, 0.6), (0.2, 0.5, 0.6, 0.3)):
+                zu = torch.empty_like(z)
+                zu[0], zu[1], zu[2], zu[3] = u, v, w, s
+                plan.run(zu, 2, out=out)
+        plan.status()
+    torch.cuda.synchronize()
+    print("profile case done")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -711,85 +883,26 @@ def main():
     if args.experiment:
         paper_experiments(args.experiment)
         return
+    if args.profile_case:
+        profile_case(args)
+        return
     ws, rank, local = dist_env()
     import torch
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_1309_1720_gb300 import Plan, api, inputs as I
+    from paper_1309_1720_gb300 import Plan, api, autotune, inputs as I
 
-    prob = api.Problem(model=api.FHN, nx=NX, ny=NY, dx=0.04, stencil=api.STENCIL9, alpha_d=1 / 6,
-                       scheme=api.RK4, dt=DT)
-    z0_host = I.fhn_broken_wave(NX, NY, seed=0)
+    prob = headline_problem(api)
+    z0_host = headline_state(I)
     z0 = torch.from_numpy(z0_host).cuda()
-    tuning = None
-    if args.profile_case:
-        # the launch shape the bench itself chose, if it ran before on this machine
-        from paper_1309_1720_gb300 import autotune
-        plan = autotune.plan_for([prob], autotune.cached([prob]))
-    else:
-        # launch shape chosen by the project's autotuner on a short run of the
-        # same workload (cached per GPU / model / size class)
-        from paper_1309_1720_gb300 import autotune
-        tuning = autotune.tune([prob], z0, n_steps=200)
-        plan = autotune.tuned_plan([prob], z0, n_steps=200)
+    # launch shape chosen by the project's autotuner on a short run of the
+    # same workload (cached per GPU / model / size class)
+    tuning = autotune.tune([prob], z0, n_steps=10)
+    plan = autotune.plan_for([prob], tuning)
     out = torch.empty_like(z0)
-    ws_t = plan.workspace()
-
-    if args.profile_case == "c1":
-        cp = api.Problem(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
-        plan = Plan(cp, tuning=dict(schedule=2, rows=4, threads=512))
-        z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
-        for _ in range(2):
-            plan.run(z, 200)
-        plan.status()
-        torch.cuda.synchronize()
-        print("profile case done")
-        return
-    if args.profile_case in ("tlm", "adj"):
-        n = 512
-        gp = api.Problem(model=api.FHN, nx=n, ny=n, dx=0.04, scheme=api.RK4, dt=2.5e-4)
-        plan = Plan(gp)
-        z = torch.from_numpy(I.fhn_broken_wave(n, n, seed=0)).cuda()
-        for _ in range(2):
-            if args.profile_case == "tlm":
-                dz0 = torch.from_numpy(np.stack([I.unit_direction(z.shape, 2, offset=i * z.numel())
-                                                 for i in range(64)])).cuda()
-                plan.tlm(z, dz0, 4)
-            else:
-                plan.adjoint(z, z.clone(), 16)
-        plan.status()
-        torch.cuda.synchronize()
-        print("profile case done")
-        return
-    if args.profile_case:
-        if args.profile_case == "bocf":
-            # four-field 2048^2 anisotropic 9-point RK4: 640 MB working set
-            n = 2048
-            bp = api.Problem(model=api.BOCF, nx=n, ny=n, dx=0.03, D=(1.171e-3,), Dyy=(1.171e-3 / 4,),
-                             stencil=api.STENCIL9, scheme=api.RK4, dt=0.05)
-            plan = autotune.plan_for([bp], autotune.cached([bp]))
-            z0 = torch.from_numpy(I.bocf_spiral_cores(n, n, seed=0)).cuda()
-            out = torch.empty_like(z0)
-            steps = 2
-        elif args.profile_case == "karma":
-            # Karma 2048^2 5-point RK4 (the launch shape its bench row uses)
-            n = 2048
-            kp = api.Problem(model=api.KARMA, nx=n, ny=n, dx=I.KARMA_DX, D=(I.KARMA_GAMMA,), scheme=api.RK4,
-                             dt=0.05)
-            plan = autotune.plan_for([kp], autotune.cached([kp]))
-            z0 = torch.from_numpy(I.karma_broken_wave(n, n, seed=0)).cuda()
-            out = torch.empty_like(z0)
-            steps = 10
-        else:
-            steps = 20
-        for _ in range(2):
-            plan.run(z0, steps, out=out)
-        plan.status()
-        torch.cuda.synchronize()
-        print("profile case done")
-        return
+    plan.workspace()
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -825,17 +938,17 @@ def main():
     tot = max_over_ranks(sum(secs), ws)
     value = replica_throughput(cells * args.steps, ws, tot)
     launch_s = statistics.median(secs)
-    achieved_tflops = FLOPS_PER_CELL_UPDATE * cells / launch_s / 1e12
 
     # end to end through the C ABI with host buffers (cg_run_host): each
     # step copies the state in from pinned host memory, runs, copies the
     # result out and reads the device status word back
+    e2e_steps = min(args.steps, 3)
     h_in = torch.from_numpy(z0_host).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     plan.run_host(h_in, 1, out=h_out, stream=stream)
     barrier()
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -846,12 +959,36 @@ def main():
     barrier()
     e2e_tot = max_over_ranks(sum(a.elapsed_time(b) / 1e3 for a, b in e2e_t), ws)
     nbytes = z0.numel() * 8
+    del h_in, h_out
+
+    # branch mix of the local terms over one whole run (outside the timed
+    # region): the voltage of every cell every 250 steps, classified by its
+    # switch state
+    params = api.default_params(api.BOCF)
+    lo, hi = bocf_branch_bounds(params)
+    every = 250
+    counts = {"rest": 0, "excited": 0}
+    n_seen = 0
+    zc = z0.clone()
+    zn = torch.empty_like(zc)
+    for _ in range(STEPS_PER_RUN // every):
+        counts["rest"] += int((zc[0] <= lo).sum())
+        counts["excited"] += int((zc[0] >= hi).sum())
+        n_seen += zc[0].numel()
+        plan.run(zc, every, out=zn, stream=stream)
+        zc, zn = zn, zc
+    plan.status()
+    mix = {"rest": counts["rest"] / n_seen, "excited": counts["excited"] / n_seen}
+    mix["general"] = 1.0 - mix["rest"] - mix["excited"]
+    del zc, zn
+    flops_cu = bocf_flops_per_cell_update(mix)
+    achieved_tflops = flops_cu * cells / launch_s / 1e12
 
     rows = None
     if not args.no_rows and rank == 0:
-        rows = secondary_rows(torch, Plan, I, api, peak_tflops)
+        rows = secondary_rows(torch, Plan, I, api, peak_tflops, tuning)
     cpu = None
-    if not args.no_cpu and rank == 0 and ws >= 1 and args.gpus == 1:
+    if not args.no_cpu and rank == 0 and args.gpus == 1:
         cpu = cpu_baseline()
 
     if rank == 0:
@@ -863,16 +1000,21 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops,
                          "traffic": MEASURED_DRAM_BYTES_PER_CELL_UPDATE * cells,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 20-step "
-                                           "launch (profiles/k_stage_fhn_1024x1024_9pt_rk4.md), scaled to "
-                                           "the 10000-step launch",
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 2-step launch of "
+                                           "this workload in its tuned launch shape (508.8 B per cell-update), "
+                                           "scaled to the 5000-step launch; the kernel is bound by the FP64 pipe, "
+                                           "not HBM",
                          "peak_source": "measured FP64 DFMA throughput of this GPU (library probe, 8 chains x "
                                         "256 threads x 4 blocks/SM), FMA = 2 flops",
-                         "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                         "flops_per_cell_update": flops_cu,
+                         "flops_per_stage_by_branch": BOCF_STAGE_FLOPS,
+                         "branch_mix": mix,
+                         "branch_mix_sample": "voltage of all cells every %d steps of one whole run" % every,
                          "hbm_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
-                         "kernel": "k_stage<FHN, 9-point, RK4> (persistent)", "tuning": tuning},
-            "e2e": {"value": ws * cells * args.steps / e2e_tot / 1e9, "unit": "GCUPS",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 4,
+                         "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * cells / launch_s / 1e9,
+                         "kernel": "k_stage<BOCF, 9-point anisotropic, RK4> (persistent)", "tuning": tuning},
+            "e2e": {"value": ws * cells * e2e_steps / e2e_tot / 1e9, "unit": "GCUPS",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 4, "steps": e2e_steps,
                     "call": "cg_run_host (pinned host state in and out, status word read back)"},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),

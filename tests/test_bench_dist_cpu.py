@@ -70,6 +70,6 @@ def test_reference_arm_json_contract():
               "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["unit"] == "GCUPS" and d["dtype"] == "f64" and d["value"] > 0
-    assert d["config"]["workload"] == "fhn-1024x1024-9pt-rk4-10000steps"
+    assert d["config"]["workload"] == "bocf-2048x2048-aniso9pt-rk4-5000steps"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
