@@ -160,6 +160,7 @@ struct cg_plan_s {
     // temporal blocking of cg_run (tuning.schedule = 2): steps per pass (0 =
     // off), tile size, tiles along x, blocks, threads, window cells, kernel
     int32_t tb_k = 0, tb_tx = 0, tb_ty = 0, tb_tiles = 0, tb_blocks = 0, tb_threads = 0, tb_wmax = 0;
+    int32_t tb_nbr = 0, tb_tiles_x = 0, tb_tiles_y = 0;   // neighbour waits between passes (one instance)
     size_t tb_smem = 0;
     const void *tb_kernel = nullptr;
     int nblocks = 0;
@@ -686,8 +687,14 @@ cg_status tb_setup(cg_plan_s *P)
             int occ = 0;
             const cg_status st = occupancy(smem, occ);
             if (st != CG_OK) return st;
-            if (occ >= 1 && ntiles <= (int64_t)occ * P->num_sms)
+            if (occ >= 1 && ntiles <= (int64_t)occ * P->num_sms) {
+                // CG_FLAG_NEIGHBOR_SYNC: each block waits between passes
+                // for the tiles its window covers only (one flag per tile)
+                P->tb_tiles_x = (nx + tx - 1) / tx;
+                P->tb_tiles_y = (ny + ty - 1) / ty;
+                P->tb_nbr = ((P->flags & CG_FLAG_NEIGHBOR_SYNC) && ntiles <= cgk::MAX_FLAG_BLOCKS) ? 1 : 0;
                 return finish(tx, ty, wmax, ntiles, (int)ntiles, smem);
+            }
             // too many tiles to be resident together: make them larger
             if (tx < nx && (tx <= ty || ty >= ny)) ++tx;
             else if (ty < ny) ++ty;
@@ -952,6 +959,9 @@ cg_status launch_stages(cg_plan P, const void *kernel, void **args, RunArgs &a, 
     a.g_begin = g0;
     a.g_end = g1;
     a.nblocks_expect = (uint32_t)P->nblocks;
+    // neighbour waits count stages in 32-bit flags: longer launches take
+    // the grid barrier (64-bit arrival counter)
+    if (a.sync_mode == cgk::SYNC_NEIGHBOR && g1 - g0 >= ((int64_t)1 << 31)) a.sync_mode = cgk::SYNC_GRID;
     if (a.sync_mode == cgk::SYNC_NEIGHBOR) {
         e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned) * (size_t)P->nblocks, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(flags)");
@@ -1177,11 +1187,24 @@ cg_status run_impl(cg_plan plan, const double *z_in, double *z_out, const double
         t.k = plan->tb_k;
         t.wmax = plan->tb_wmax;
         t.n_steps = n_steps;
+        const int64_t n_pass = (n_steps + plan->tb_k - 1) / plan->tb_k;
+        // pass counts are 32-bit flags: longer runs take the grid barrier
+        t.nbr = (plan->tb_nbr && n_pass < ((int64_t)1 << 31)) ? 1 : 0;
+        t.tiles_x = plan->tb_tiles_x;
+        t.tiles_y = plan->tb_tiles_y;
+        {
+            const int H = plan->tb_k * plan->ns;
+            t.rx = (H + plan->tb_tx - 1) / plan->tb_tx;
+            t.ry = (H + plan->tb_ty - 1) / plan->tb_ty;
+        }
         a.persistent = 1;
         a.nblocks_expect = (uint32_t)plan->tb_blocks;
         a.stuck_barrier = (plan->flags & CG_FLAG_TEST_STUCK_BARRIER) ? 1u : 0u;
-        e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(barrier)");
+        if (t.nbr)
+            e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned) * (size_t)plan->tb_blocks, s);
+        else
+            e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(pass synchronisation)");
         void *targs[] = {&a, &t};
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof cfg);

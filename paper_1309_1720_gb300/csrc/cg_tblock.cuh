@@ -16,6 +16,13 @@
 // values from another tile between barriers, and no stage needs a separate
 // ghost refill.
 //
+// Between passes the blocks synchronise either with the grid barrier or,
+// for a single instance, with neighbour waits: a block publishes how many
+// passes it has finished and, before the next one, waits only for the tiles
+// whose cells its window covers (they write what it reads next, and read
+// what it overwrites next), so blocks drift against distant tiles and no
+// grid-wide round trip is paid.
+//
 // Each cell's arithmetic is the stage kernel's: the model's local terms with
 // the centre weight folded in, the off-centre sums in the same order (5-point:
 // wy (S + N) then wx (W + E); 9-point: row sums R = W + E and
@@ -33,8 +40,60 @@ struct TbArgs {
     int32_t n_tiles;         // tiles of all instances (instance i owns [tb_tile_begin, + tb_tiles))
     int32_t k;               // steps per pass
     int32_t wmax;            // shared window capacity in cells (per array)
+    int32_t nbr;             // 1: neighbour waits between passes (single instance, one tile per block)
+    int32_t tiles_x, tiles_y;   // tile grid of the single instance (neighbour waits)
+    int32_t rx, ry;          // a window covers tiles within rx columns and ry rows of its own
     int64_t n_steps;
 };
+
+// Neighbour synchronisation between passes (single instance, tile b on
+// block b): publish `done` passes, then wait (bounded) until every tile
+// within rx columns and ry rows has published `need`.  The lanes of warp 0
+// poll up to 32 flags at once.  On expiry the block records CG_DEV_TIMEOUT
+// and every thread returns false.
+static __device__ __noinline__ bool tb_neighbor_sync(unsigned *flags, uint32_t *status, uint64_t timeout_ns,
+                                                     unsigned done, unsigned need, const TbArgs &t)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) {
+            // the block's stores of this pass, ordered before by
+            // __syncthreads, become visible with the release
+            __threadfence();
+            st_release_u32(flags + blockIdx.x, done);
+        }
+        __syncwarp();
+        const int bx = (int)blockIdx.x % t.tiles_x, by = (int)blockIdx.x / t.tiles_x;
+        const int x0 = max(bx - t.rx, 0), x1 = min(bx + t.rx, t.tiles_x - 1);
+        const int y0 = max(by - t.ry, 0), y1 = min(by + t.ry, t.tiles_y - 1);
+        const int w = x1 - x0 + 1, cnt = w * (y1 - y0 + 1);
+        int ok = 1;
+        const uint64_t t0 = global_timer_ns();
+        const uint64_t max_iter = (timeout_ns >> 5) + (1ull << 20);
+        uint64_t it = 0;
+        for (int base = 0; base < cnt && ok; base += 32) {
+            const int j = base + lane;
+            const unsigned *f = flags + ((j < cnt) ? (y0 + j / w) * t.tiles_x + (x0 + j % w) : (int)blockIdx.x);
+            for (;;) {
+                const bool ready = ld_acquire_u32(f) >= need;
+                if (__all_sync(CG_FULL, ready)) break;
+                __nanosleep(32);
+                const bool expired = (++it & 63) == 0 && (global_timer_ns() - t0 > timeout_ns || it > max_iter);
+                if (__any_sync(CG_FULL, expired)) {
+                    ok = 0;
+                    if (lane == 0) atomicOr(status, CG_DEV_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (lane == 0) s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 // Output buffer of an instance in pass p of P: the last pass writes its
 // output, except in place (input == output) where the first pass must not
@@ -203,13 +262,22 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             const int w = exh - exl, n = w * (eyh - eyl);
             double *Yout = (NS == 1) ? ((Yin == YA) ? YB : YA) : (last ? Z : ((s & 1) ? YB : YA));
             const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
-            // every thread runs the same number of iterations, so the
-            // model's warp-uniform paths see whole warps; surplus threads
-            // repeat the last cell and store nothing
+            // Rounds of up to blockDim cells, cell c of a round on thread c.
+            // The FP64 pipe takes a warp instruction in the same time
+            // whether 1 or 32 lanes are active, so cells are packed into as
+            // few warps as possible (a warp issues on sub-partition
+            // warp mod 4: consecutive warps spread over the four).  A warp
+            // with no cell skips the round (warp-uniform); in the others
+            // every lane runs, so the model's warp-uniform paths see whole
+            // warps: surplus lanes repeat the round's last cell and store
+            // nothing.
+            const int wid = (int)(threadIdx.x >> 5);
             for (int base = 0; base < n; base += blockDim.x) {
+                const int m = min(n - base, (int)blockDim.x);
+                if ((wid << 5) >= m) continue;
                 const int c = base + (int)threadIdx.x;
-                const bool act = c < n;
-                const int cc = act ? c : n - 1;
+                const bool act = c < base + m;
+                const int cc = act ? c : base + m - 1;
                 const int gx = exl + cc % w, gy = eyl + cc / w;
                 const int sx = map_idx(gx, nx, bc), sy = map_idx(gy, ny, bc);   // identity inside the grid
                 int li = at(gx, gy), ls = at(sx, sy);
@@ -289,8 +357,11 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
 
     auto pass_end = [&](int64_t p) {
         if (p + 1 < P) {
-            const unsigned long long target = (unsigned long long)(p + 1) * a.nblocks_expect +
-                                              ((p == 0 && a.stuck_barrier) ? 1u : 0u);
+            const unsigned extra = (p == 0 && a.stuck_barrier) ? 1u : 0u;
+            if (t.nbr)
+                return tb_neighbor_sync(a.flags, a.status, a.timeout_ns, (unsigned)(p + 1), (unsigned)(p + 1) + extra,
+                                        t);
+            const unsigned long long target = (unsigned long long)(p + 1) * a.nblocks_expect + extra;
             return grid_barrier(reinterpret_cast<unsigned long long *>(a.sync), a.status, a.timeout_ns, target);
         }
         return true;

@@ -145,3 +145,59 @@ def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
     per_block = np.array([cost[flat == b].sum() for b in range(G)])
     if nx * ny >= 4 * G:
         assert per_block.max() - per_block.min() <= 2.8 + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Temporally blocked kernel (cg_tblock.cuh): the index arithmetic of its
+# stage rounds and of its neighbour waits, restated here and checked before
+# it runs on a GPU.
+
+def _stage_round_cells(threads, m):
+    """Cell of each thread in a round of m cells (-1: surplus lane, -2: warp
+    skips the round), as the stage loop of k_tblock assigns them."""
+    tid = np.arange(threads)
+    wid = tid >> 5
+    out = np.where(tid < m, tid, -1)
+    out[(wid << 5) >= m] = -2
+    return out
+
+
+@pytest.mark.parametrize("threads", [64, 96, 128, 256, 384, 512])
+def test_tblock_stage_rounds_cover_once(threads):
+    """Every cell of a round goes to exactly one active lane, packed into
+    ceil(m/32) warps (the FP64 pipe costs a whole warp per instruction
+    however many lanes are active); the other warps skip the round."""
+    for m in range(1, threads + 1):
+        cells = _stage_round_cells(threads, m)
+        act = cells[cells >= 0]
+        assert np.array_equal(np.sort(act), np.arange(m)), m
+        running = [w for w in range(threads // 32) if not (cells[32 * w:32 * w + 32] == -2).all()]
+        assert len(running) == (m + 31) // 32, m
+        for w in running:
+            assert (cells[32 * w:32 * w + 32] >= 0).any(), (m, w)
+
+
+def _tb_window(t0, t1, n, h):
+    return (-1 if t0 - h <= 0 else t0 - h), (n + 1 if t1 + h >= n else t1 + h)
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 45, 128, 301])
+@pytest.mark.parametrize("tx", [1, 2, 5, 11, 16, 64])
+@pytest.mark.parametrize("H", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_tblock_neighbour_ranges(n, tx, H, bc):
+    """A tile's window (tile plus H cells, ghosts at the edges read from the
+    cells they mirror or repeat) lies in the tiles within ceil(H/tx) of it,
+    the range a block waits for between passes."""
+    tiles = (n + tx - 1) // tx
+    r = (H + tx - 1) // tx
+    for b in range(tiles):
+        w0, w1 = _tb_window(b * tx, min(b * tx + tx, n), n, H)
+        for g in range(w0, w1):
+            if g < 0:
+                src = (1 if n > 1 else 0) if bc == 0 else 0
+            elif g >= n:
+                src = (n - 2 if n > 1 else 0) if bc == 0 else n - 1
+            else:
+                src = g
+            assert abs(src // tx - b) <= r, (b, g, src)

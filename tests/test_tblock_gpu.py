@@ -133,6 +133,69 @@ def test_tblock_device_checks(cuda_ok):
                           _run(p, _state(FHN, 64, 64), 6))
 
 
+@pytest.mark.parametrize("model", [0, 1, 3])
+@pytest.mark.parametrize("scheme", [0, 2])
+@pytest.mark.parametrize("shape", [(128, 128), (67, 45), (3, 7), (2, 2), (512, 2), (300, 17)])
+def test_tblock_neighbor_sync_bitwise(cuda_ok, model, scheme, shape):
+    """Neighbour waits between passes (each block waits for the tiles its
+    window covers, not for the whole grid): results equal the stage
+    kernel's bit for bit for several steps per pass and block sizes (a
+    multiple of four warps deals cells to sub-partitions, three warps do
+    not), out of place and in place."""
+    from paper_1309_1720_gb300 import CGError, FLAG_NEIGHBOR_SYNC
+    nx, ny = shape
+    p = _problem(model, nx, ny, 1, scheme, 0)
+    z0 = _state(model, nx, ny)
+    n = 9
+    ref = _run(p, z0, n)
+    q = _problem(model, nx, ny, 1, scheme, 0)
+    q.flags = FLAG_NEIGHBOR_SYNC
+    ran = 0
+    for k, thr in ((1, 256), (2, 512), (4, 128), (3, 384), (2, 96)):
+        try:
+            g = _run(q, z0, n, tuning=dict(schedule=2, rows=k, threads=thr))
+        except CGError as e:
+            # a tile and its halo that do not fit shared memory (four-field
+            # RK4 with deep passes) are refused at plan creation
+            assert e.status == 7, e
+            continue
+        assert np.array_equal(g, ref), (k, thr)
+        ran += 1
+    assert ran >= 3
+    assert np.array_equal(_run(q, z0, n, tuning=dict(schedule=2, rows=1), inplace=True), ref)
+
+
+def test_tblock_neighbor_sync_c1_and_timeout(cuda_ok):
+    """The 128^2 Euler workload with neighbour waits, 1000 steps, against the
+    stage kernel and the oracle; and the testing knob: the first wait
+    expects a pass that never comes, gives up after 0.2 s with
+    CG_ETIMEOUT, and the context stays usable."""
+    import torch
+    from paper_1309_1720_gb300 import CGError, Plan, FHN, FLAG_NEIGHBOR_SYNC, FLAG_TEST_STUCK_BARRIER
+    p = _problem(FHN, 128, 128, 0, 0, 0)
+    p.dt = 2e-4
+    z0 = I.fhn_broken_wave(128, 128, seed=0)
+    ref = _run(p, z0, 1000)
+    q = _problem(FHN, 128, 128, 0, 0, 0)
+    q.dt = 2e-4
+    q.flags = FLAG_NEIGHBOR_SYNC
+    for k, thr in ((4, 512), (8, 512), (2, 256)):
+        assert np.array_equal(_run(q, z0, 1000, tuning=dict(schedule=2, rows=k, threads=thr)), ref), k
+    assert field_rel_err(ref, oracle_run(p, z0, 1000)) <= TOL
+    s = _problem(FHN, 64, 64, 0, 2, 0)
+    s.flags = FLAG_NEIGHBOR_SYNC | FLAG_TEST_STUCK_BARRIER
+    s.barrier_timeout_s = 0.2
+    stuck = Plan(s, tuning=dict(schedule=2, rows=2))
+    stuck.run(torch.from_numpy(_state(FHN, 64, 64)).cuda(), 6)
+    with pytest.raises(CGError) as ei:
+        stuck.status()
+    assert ei.value.status == 6                      # CG_ETIMEOUT
+    good = _problem(FHN, 64, 64, 0, 2, 0)
+    good.flags = FLAG_NEIGHBOR_SYNC
+    assert np.array_equal(_run(good, _state(FHN, 64, 64), 6, tuning=dict(schedule=2, rows=2)),
+                          _run(good, _state(FHN, 64, 64), 6))
+
+
 @pytest.mark.parametrize("model", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_tblock_batch_bitwise(cuda_ok, model, k):
