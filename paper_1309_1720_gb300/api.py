@@ -134,6 +134,7 @@ class Plan:
         L = _lib.lib()
         single = isinstance(problems, Problem)
         self.problems = [problems] if single else list(problems)
+        self.tuning = dict(tuning) if tuning else None
         self.model = self.problems[0].model
         self.nv = n_fields(self.model)
         cprobs = (CProblem * len(self.problems))(*[p.to_c() for p in self.problems])

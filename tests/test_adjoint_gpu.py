@@ -189,7 +189,9 @@ def test_state_only_adjoint_same_lam0(cuda_ok, model, stencil):
         assert d1 is None and d0.shape[0] >= 1
         assert torch.equal(a0, a1)
         lam[every] = a0
-    D = torch.zeros(d0.shape[0], dtype=torch.float64, device="cuda")     # no gradient wanted
+    # the plan's own diffusivities, no gradient wanted
+    D = torch.tensor(autograd._plan_D(plan), dtype=torch.float64, device="cuda")
+    assert D.shape[0] == d0.shape[0]
     z = z0.clone().requires_grad_(True)
     autograd.flow(z, D, plan, 12).mul(lamT).sum().backward()
     assert torch.equal(z.grad, lam[0])

@@ -116,3 +116,47 @@ def test_autograd_flow(cuda_ok):
         return float(torch.sum((q.run(z0.detach(), steps)[0] - u_tgt) ** 2))
     fd = (L_of(1 + eps) - L_of(1 - eps)) / (2 * eps)
     assert abs(float(D.grad[0]) - fd) <= 1e-8 * abs(fd)
+
+
+def test_autograd_flow_follows_D(cuda_ok):
+    """The differentiable flow runs with the D it is given: with D unlike the
+    plan's, the forward equals a plan built with that D bit for bit, the
+    gradients equal that plan's adjoint, and dL/dD matches central
+    differences; D back at the plan's values runs the plan itself."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, Problem, FHN, BOCF, RK4, STENCIL9
+    from paper_1309_1720_gb300.autograd import flow, plan_for_D
+    n, steps = 64, 80
+    base = dict(model=FHN, nx=n, ny=n + 5, dx=0.04, scheme=RK4, dt=2.5e-4)
+    plan = Plan(Problem(**base))
+    z0 = torch.from_numpy(I.fhn_broken_wave(n, n + 5, seed=3)).cuda()
+    u_tgt = Plan(Problem(D=(1.05, 1.5), **base)).run(z0, steps)[0]
+    for Dv in ((1.1, 1.4), (1.0, 1.5)):
+        D = torch.tensor(Dv, dtype=torch.float64, device="cuda", requires_grad=True)
+        z = z0.clone().requires_grad_(True)
+        zT = flow(z, D, plan, steps)
+        ref_plan = Plan(Problem(D=Dv, **base))
+        assert torch.equal(zT, ref_plan.run(z0, steps))
+        assert (plan_for_D(plan, D) is plan) == (Dv == (1.0, 1.5))
+        loss = torch.sum((zT[0] - u_tgt) ** 2)
+        loss.backward()
+        lamT = torch.zeros_like(zT)
+        lamT[0] = 2 * (zT[0].detach() - u_tgt)
+        lam0, dLdD = ref_plan.adjoint(z0, lamT, steps)
+        assert torch.equal(z.grad, lam0) and torch.equal(D.grad, dLdD)
+        eps = 1e-6
+
+        def L_of(Du):
+            q = Plan(Problem(D=(Du, Dv[1]), **base))
+            return float(torch.sum((q.run(z0, steps)[0] - u_tgt) ** 2))
+        fd = (L_of(Dv[0] + eps) - L_of(Dv[0] - eps)) / (2 * eps)
+        assert abs(float(D.grad[0]) - fd) <= 1e-8 * abs(fd)
+    # anisotropic four-field plan: the ratio Dyy/Dxx of the plan is kept
+    bp = dict(model=BOCF, nx=40, ny=33, dx=0.03, stencil=STENCIL9, scheme=RK4, dt=0.05)
+    plan_b = Plan(Problem(D=(1.171e-3,), Dyy=(1.171e-3 / 4,), **bp))
+    zb = torch.from_numpy(I.bocf_spiral_cores(40, 33, n_cores=2)).cuda()
+    Db = torch.tensor([1.3e-3], dtype=torch.float64, device="cuda")
+    out = flow(zb, Db, plan_b, 10)
+    assert torch.equal(out, Plan(Problem(D=(1.3e-3,), Dyy=(1.3e-3 / 4,), **bp)).run(zb, 10))
+    with pytest.raises(ValueError):
+        flow(zb, torch.tensor([1e-3, 1e-3], dtype=torch.float64, device="cuda"), plan_b, 10)
