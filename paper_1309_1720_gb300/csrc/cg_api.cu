@@ -1788,13 +1788,11 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
         st = launch_stages(plan, plan->kernel, args, a, 0, L.c * plan->ns, plan->nblocks, s);
         if (st != CG_OK) return st;
     }
-    // 2. lam = lamT, kb = dt b_last lamT
+    // 2. lam = lamT, kh = kbar / (dt b_last) = lamT
     double *lam = kb + 2 * L.S, *lacc = kb + 3 * L.S;
     e = cudaMemcpyAsync(lam, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kb, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam)");
-    cgk::k_scale<<<plan->num_sms * 4, 256, 0, s>>>(kb, lamT, plan->cacc[plan->ns - 1], nstate);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "scale kernel");
     // 3. segments in reverse: recompute with every stage kept, then sweep back
     int64_t r = 0;
     for (int64_t j = L.nseg - 1; j >= 0; --j) {
@@ -1813,6 +1811,8 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
             a.warp_seg = plan->d_warp_seg_adj;
         }
         cgk::AdjArgs b;
+        std::memset(&b, 0, sizeof b);
+        for (int q = 1; q < plan->ns; ++q) b.chat[q] = plan->cy[q - 1] * plan->cacc[q] / plan->cacc[q - 1];
         b.store = store;
         b.kb0 = kb;
         b.kb1 = kb + L.S;
