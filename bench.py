@@ -53,11 +53,14 @@ BYTES_PER_CELL_UPDATE = 64
 #   excited  u >= theta_v + 1/(2k): every switch is exactly 1;
 #   general  in between: the whole of Eq. (bochfe).
 # The sigmoid, exponential and reciprocal count at the flops of the
-# library's own evaluations (Tang's table-driven exponential, a cubic
-# Newton reciprocal), which take the place of the tanh and division costs
-# T and R.  Frozen from ncu's per-opcode counters (DFMA x 2 + DADD + DMUL
-# thread instructions per cell and stage) on uniform states where every
-# warp takes one branch, in the workload's tuned launch shape:
+# library's own evaluations as they stood when the count was frozen
+# (Tang's table-driven exponential with a 256-entry table: 7 FMA, 1 add,
+# 1 multiply; a cubic Newton reciprocal: 3 FMA), which take the place of
+# the tanh and division costs T and R; later changes that evaluate the same
+# functions with fewer operations show as speed, not as a lower count.
+# Frozen from ncu's per-opcode counters (DFMA x 2 + DADD + DMUL thread
+# instructions per cell and stage) on uniform states where every warp takes
+# one branch, in the workload's tuned launch shape:
 #   rest     DFMA 48.5, DADD 14.5, DMUL 13.0 -> 124.5
 #   excited  DFMA 34.5, DADD 13.5, DMUL 13.0 ->  95.5
 #   general  DFMA 71.5, DADD 23.5, DMUL 31.0 -> 197.5

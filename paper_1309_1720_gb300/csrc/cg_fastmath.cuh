@@ -10,13 +10,15 @@
 //
 // exp_neg: e^x for x <= 0, by P. T. P. Tang's table-driven method ("Table-
 // driven implementation of the exponential function in IEEE floating-point
-// arithmetic", ACM TOMS 15, 1989) with a 256-entry table:
-// x = (256 m + j) ln2/256 + r with |r| <= ln2/512, e^x = 2^m 2^(j/256) e^r,
-// e^r - 1 by its Taylor polynomial of degree 4 (remainder below
-// |r|^5/120 < 4e-17), 2^(j/256) from the table, 2^m added to the exponent
-// field.  Nine FP64 instructions.
+// arithmetic", ACM TOMS 15, 1989) with a 4096-entry table:
+// x = (4096 m + j) ln2/4096 + r with |r| <= ln2/8192, e^x = 2^m 2^(j/4096) e^r,
+// e^r - 1 by its Taylor polynomial of degree 3 (remainder below
+// |r|^4/24 < 2.2e-18), 2^(j/4096) from the table (32 KB, read through the
+// read-only cache; neighbouring cells take neighbouring entries), 2^m added
+// to the exponent field.  Eight FP64 instructions (a 256-entry table needs
+// degree 4 and nine).
 // sigmoid: 1/(1 + e^-a) = (1 + tanh(a/2))/2 from e = e^-|a| in (0, 1]:
-// 1/(1+e) for a >= 0, e/(1+e) otherwise.  Fourteen FP64 instructions; also
+// 1/(1+e) for a >= 0, e/(1+e) otherwise.  Thirteen FP64 instructions; also
 // returns s (1 - s) = e/(1+e)^2 for derivatives.
 #pragma once
 
@@ -44,29 +46,29 @@ __device__ __forceinline__ double fast_rcp(double x)
     return fma(r, fma(e, e, e), r);
 }
 
-// e^x for x <= 0 (x below -708 is treated as -708); tab[j] = 2^(j/256).
+// e^x for x <= 0 (x below -708 is treated as -708); tab[j] = 2^(j/4096).
 __device__ __forceinline__ double exp_neg(double x, const double *tab)
 {
+    static_assert(EXP_TAB == 4096, "exp_neg's constants are those of a 4096-entry table");
     const long long LIM = 0x4086200000000000ll;             // 708.0
     long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
     b = b > LIM ? LIM : b;
     x = -__longlong_as_double(b);
     const double SHIFT = 6755399441055744.0;                // 1.5 * 2^52: rounds to an integer
-    const double INV_L = 369.3299304675746;                 // 256 / ln 2
-    const double L_HI = 0.0027076061740622863;              // ln 2 / 256, leading part
-    const double L_LO = 9.058776616587108e-20;              // ln 2 / 256 - L_HI
+    const double INV_L = 5909.278887481194;                 // 4096 / ln 2
+    const double L_HI = 0.0001692253858788929;              // ln 2 / 4096, nearest double
+    const double L_LO = 5.661735385366942e-21;              // ln 2 / 4096 - L_HI
     const double t = fma(x, INV_L, SHIFT);
-    const long long n = __double_as_longlong(t) - 0x4338000000000000ll;   // round(x 256 / ln 2)
+    const long long n = __double_as_longlong(t) - 0x4338000000000000ll;   // round(x 4096 / ln 2)
     const double kd = t - SHIFT;
     double r = fma(-kd, L_HI, x);
     r = fma(-kd, L_LO, r);
-    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-    q = fma(r, q, 0.5);
+    double q = fma(r, 1.0 / 6.0, 0.5);
     q = fma(r, q, 1.0);
     const double p = r * q;                                  // e^r - 1
     const double T = __ldg(tab + (n & (EXP_TAB - 1)));
     const double e = fma(T, p, T);
-    return __longlong_as_double(__double_as_longlong(e) + ((n >> 8) << 52));
+    return __longlong_as_double(__double_as_longlong(e) + ((n >> 12) << 52));
 }
 
 // s = 1 / (1 + e^-a); ds = s (1 - s).

@@ -12,7 +12,7 @@ namespace cgk {
 
 constexpr int MAXF = 4;     // fields per cell (BOCF: u, v, w, s)
 constexpr int NMP = 64;     // model constants shared by all instances of a plan
-constexpr int EXP_TAB = 256; // entries 2^(j/256) of the exponential's table (cg_fastmath.cuh)
+constexpr int EXP_TAB = 4096; // entries 2^(j/4096) of the exponential's table (cg_fastmath.cuh)
 
 // One grid instance, resident in a plan-owned device table.  Coefficients
 // carry D/dx^2 and the stencil weights; the centre weight is folded into the
@@ -29,7 +29,7 @@ struct Inst {
     double wx[MAXF], wy[MAXF], wd[MAXF], wc[MAXF];   // off-centre / centre stencil weights
     double wt[MAXF];         // wy / wd (0 where wd = 0): the 9-point stencil's row-sum form
     double mi[4];            // instance-dependent folds of centre weight and model constants
-    const double *tab;       // plan-owned table 2^(j/256), j = 0..255 (exponentials)
+    const double *tab;       // plan-owned table 2^(j/4096), j = 0..4095 (exponentials)
 };
 
 // A warp's share of one stage under the static schedule: columns
