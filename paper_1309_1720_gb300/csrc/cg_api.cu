@@ -168,7 +168,7 @@ struct cg_plan_s {
     std::vector<int2> deps;          // halo owners of each block (neighbour sync)
     int2 *d_deps = nullptr;
     int32_t sync_mode = cgk::SYNC_GRID;
-    double *d_tab = nullptr;         // 2^(j/256) table of the exponential
+    double *d_tab = nullptr;         // 2^(j/4096) table of the exponential
     // workspace and stream of the latest run issued with this plan (for
     // cg_get_device_status; the plan's numerical content stays immutable)
     std::mutex last_mu;
@@ -429,6 +429,12 @@ void fold_constants(cg_plan_s &P, const cg_problem &p, Inst &I)
                                        first_one(P.mp[cgk::BD_CVM]), first_one(P.mp[cgk::BD_CO])});
         P.mp[cgk::BD_KREST] = key_bits(u_rest);
         P.mp[cgk::BD_KEXC] = key_bits(u_exc);
+        {
+            // exact savings the constants allow (cg_stepper.cuh, BF_*)
+            long long fl = 0;
+            if (std::memcmp(&P.mp[cgk::BD_CVM], &P.mp[cgk::BD_CO], sizeof(double)) == 0) fl |= cgk::BF_SAME_VMO;
+            std::memcpy(&P.mp[cgk::BD_FLAGS], &fl, sizeof fl);
+        }
         static_assert(cgk::BD_N <= cgk::NMP, "model constant table too small");
         I.mi[0] = I.wc[0];
     }
