@@ -41,6 +41,11 @@ DEFAULT_CANDIDATES: List[Dict] = [
     dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=2),
     dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=1, rows=8),
     dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=4),
+    # taller queue tiles: fewer window start-up rows per tile (row sums of
+    # the 9-point stencil are formed for 2 extra rows per tile)
+    dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=8),
+    dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=16),
+    dict(cells_x=1, threads=256, blocks_per_sm=2, schedule=1, rows=8),
     dict(cells_x=2, threads=512, blocks_per_sm=1, schedule=0, sync="per_stage"),
     # fewer, longer warp shares: the 9-point window's start-up rows are
     # amortised over more rows, at lower occupancy

@@ -7,8 +7,9 @@ contraction, summation order and libm-vs-CUDA transcendental rounding.
 import numpy as np
 import pytest
 
-from helpers import field_rel_err, gpu_run, oracle_run
+from helpers import field_rel_err, gpu_run, oracle_problem, oracle_run
 from paper_1309_1720_gb300 import inputs as I
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -108,8 +109,8 @@ def test_c2_first_100_steps(cuda_ok):
 def test_c3_sampled_windows_100_steps(cuda_ok):
     """2048^2 four-field model, anisotropic 9-point, RK4, the first 100 steps
     of the 5000-step workload, with the library's default launch shape, the
-    tile-queue shape the autotuner picks for the bench and neighbour-only
-    synchronisation: the oracle recomputes windows whose margin (4 cells
+    tile-queue shapes the autotuner chooses among for the bench and
+    neighbour-only synchronisation: the oracle recomputes windows whose margin (4 cells
     per step: one per RK stage) covers the domain of dependence, so each
     window's interior is exact; windows at the four corners, on the edges
     and in the interior (six oracle runs in parallel threads)."""
@@ -134,8 +135,9 @@ def test_c3_sampled_windows_100_steps(cuda_ok):
     for t in threads:
         t.join()
     assert len(ref) == len(corners)
-    shapes = [(p, None), (p, dict(cells_x=1, threads=512, blocks_per_sm=1, schedule=1, rows=4)),
-              (_bocf(n, n, flags=FLAG_NEIGHBOR_SYNC), dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=0))]
+    shapes = [(p, None)] + [(p, dict(cells_x=1, threads=thr, blocks_per_sm=bps, schedule=1, rows=r))
+                            for thr, bps, r in ((512, 1, 4), (512, 1, 8), (512, 1, 16), (256, 2, 8))] + \
+             [(_bocf(n, n, flags=FLAG_NEIGHBOR_SYNC), dict(cells_x=2, threads=256, blocks_per_sm=2, schedule=0))]
     for q, tuning in shapes:
         g = gpu_run(q, z0, steps, tuning=tuning)
         for (y0, x0) in corners:
@@ -211,3 +213,29 @@ def test_barrier_timeout_reports_status(cuda_ok):
     g = gpu_run(q, I.fhn_broken_wave(64, 64), 3)
     o = oracle_run(q, I.fhn_broken_wave(64, 64), 3)
     assert field_rel_err(g, o) <= TOL
+
+
+@pytest.mark.parametrize("scheme", [0, 2])
+@pytest.mark.parametrize("tho", [0.02, 0.0061])
+def test_bocf_distinct_switch_thresholds(cuda_ok, scheme, tho):
+    """Constants with theta_o != theta_v^- (0.006): the plan evaluates the
+    v^- and o switches apart (it shares them only when the two switch
+    constants are equal bit for bit).  Forward, tangent-linear and adjoint
+    against the oracle on a ragged grid, 1e-12."""
+    import torch
+    from paper_1309_1720_gb300 import Plan, BOCF, default_params
+    prm = default_params(BOCF)
+    prm[5] = tho
+    p = _bocf(67, 45, params=prm, scheme=scheme)
+    z0 = I.bocf_spiral_cores(67, 45, n_cores=2)
+    op = oracle_problem(p)
+    assert field_rel_err(gpu_run(p, z0, 60), O.step(op, z0, 60)) <= TOL
+    plan = Plan(p)
+    dz0 = I.unit_direction(z0.shape, 41)
+    zT, dzT = plan.tlm(torch.from_numpy(z0).cuda(), torch.from_numpy(dz0[None].copy()).cuda(), 20)
+    plan.status()
+    assert field_rel_err(dzT[0].cpu().numpy(), O.tlm(op, z0, dz0, 20)[1]) <= TOL
+    lamT = I.unit_direction(z0.shape, 42)
+    lam0, _ = plan.adjoint(torch.from_numpy(z0).cuda(), torch.from_numpy(lamT).cuda(), 20)
+    plan.status()
+    assert field_rel_err(lam0.cpu().numpy(), O.adjoint(op, z0, lamT, 20)[0]) <= TOL
