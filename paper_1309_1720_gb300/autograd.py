@@ -62,8 +62,10 @@ def plan_for_D(plan, D: torch.Tensor):
         new_xx[i], new_yy[i] = d, d * ratio
     q = dataclasses.replace(p, D=tuple(new_xx), Dyy=tuple(new_yy), _keep=[])
     cache[key] = api.Plan(q, tuning=plan.tuning)
+    # evicted plans are not closed here: a pending backward may still hold
+    # one (its autograd context keeps a reference); they close when freed
     while len(cache) > _MAX_CACHED:
-        cache.popitem(last=False)[1].close()
+        cache.popitem(last=False)
     return cache[key]
 
 

@@ -151,6 +151,20 @@ def test_autograd_flow_follows_D(cuda_ok):
             return float(torch.sum((q.run(z0, steps)[0] - u_tgt) ** 2))
         fd = (L_of(Dv[0] + eps) - L_of(Dv[0] - eps)) / (2 * eps)
         assert abs(float(D.grad[0]) - fd) <= 1e-8 * abs(fd)
+    # more distinct D values than the plan keeps, all forwards first: every
+    # backward still runs on the plan of its own D
+    outs = []
+    for j in range(6):
+        Dj = torch.tensor((1.0 + 0.02 * (j + 1), 1.5), dtype=torch.float64, device="cuda", requires_grad=True)
+        zj = z0.clone().requires_grad_(True)
+        outs.append((Dj, zj, flow(zj, Dj, plan, 10)))
+    for j, (Dj, zj, oj) in enumerate(outs):
+        oj[0].sum().backward()
+        ref_plan = Plan(Problem(D=(1.0 + 0.02 * (j + 1), 1.5), **base))
+        lam = torch.zeros_like(oj)
+        lam[0] = 1.0
+        l0, dd = ref_plan.adjoint(z0, lam, 10)
+        assert torch.equal(zj.grad, l0) and torch.equal(Dj.grad, dd), j
     # anisotropic four-field plan: the ratio Dyy/Dxx of the plan is kept
     bp = dict(model=BOCF, nx=40, ny=33, dx=0.03, stencil=STENCIL9, scheme=RK4, dt=0.05)
     plan_b = Plan(Problem(D=(1.171e-3,), Dyy=(1.171e-3 / 4,), **bp))
