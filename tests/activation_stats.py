@@ -27,8 +27,10 @@ class ActivationStats:
         self.u_prev = np.array(u0, dtype=np.float64, copy=True)
         self.above = self.u_prev > self.theta
         self.last_up = np.full(self.u_prev.shape, np.nan)
+        self.last_dn = np.full(self.u_prev.shape, np.nan)
+        self.di_up = np.full(self.u_prev.shape, np.nan)     # diastolic interval before the current beat
         self.n_up = np.zeros(self.u_prev.shape, dtype=np.int64)
-        self.apd, self.cl = [], []
+        self.apd, self.cl, self.di = [], [], []
 
     def add(self, u: np.ndarray, t: float) -> None:
         u = np.asarray(u, dtype=np.float64)
@@ -42,6 +44,8 @@ class ActivationStats:
             t_a = self.last_up[dn]
             ok = np.isfinite(t_a) & (t_a >= lo) & (t_a <= hi)
             self.apd.append((t_dn - t_a)[ok])
+            self.di.append(self.di_up[dn][ok])
+            self.last_dn[dn] = t_dn
         up = ~self.above & now_above
         if up.any():
             t_up = t_prev + (th - up_prev[up]) / (u[up] - up_prev[up]) * dts
@@ -51,6 +55,7 @@ class ActivationStats:
             inwin = (t_up >= lo) & (t_up <= hi)
             idx = np.flatnonzero(up)
             self.n_up.flat[idx[inwin]] += 1
+            self.di_up[up] = t_up - self.last_dn[up]
             self.last_up[up] = t_up
         self.above = now_above
         self.u_prev = u.copy()
@@ -65,13 +70,47 @@ class ActivationStats:
                     "p50": float(np.percentile(x, 50)), "p90": float(np.percentile(x, 90))}
         return {"apd": q(self.apd), "interval": q(self.cl),
                 "activations_per_cell": float(self.n_up.mean()),
-                "active_fraction": float((self.n_up > 0).mean())}
+                "active_fraction": float((self.n_up > 0).mean()),
+                "restitution": self.restitution()}
+
+    def restitution(self, width: float = 5.0, n_bins: int = 40) -> dict:
+        """APD restitution: the mean action-potential duration of the beats
+        whose preceding diastolic interval (the previous repolarisation to
+        this activation) falls in [k width, (k + 1) width), with the beat
+        count per bin (beats with a known interval only)."""
+        apd = np.concatenate(self.apd) if self.apd else np.zeros(0)
+        di = np.concatenate(self.di) if self.di else np.zeros(0)
+        ok = np.isfinite(di)
+        apd, di = apd[ok], di[ok]
+        k = np.floor(di / width).astype(np.int64)
+        out = {"width": width, "n": [], "mean_apd": []}
+        for b in range(n_bins):
+            m = k == b
+            out["n"].append(int(m.sum()))
+            out["mean_apd"].append(float(apd[m].mean()) if m.any() else None)
+        return out
 
 
-def compare(a: dict, b: dict, rel: float = 0.01, rel_tail: float = None) -> list:
-    """Names of the statistics of b that differ from a's by more than rel
-    (relative to a's; percentiles relative to a's median); the 90%
-    quantiles by more than rel_tail (default rel)."""
+def compare_restitution(a: dict, b: dict, rel: float = 0.01, min_share: float = 0.01) -> list:
+    """Bins (by index) whose mean APD differs by more than rel between a and
+    b, among the bins holding at least min_share of a's beats."""
+    tot = sum(a["n"])
+    bad = []
+    for k, (na, ma, mb) in enumerate(zip(a["n"], a["mean_apd"], b["mean_apd"])):
+        if tot == 0 or na < min_share * tot:
+            continue
+        if mb is None or abs(mb - ma) > rel * abs(ma):
+            bad.append(k)
+    return bad
+
+
+def compare(a: dict, b: dict, rel: float = 0.01, rel_mean: float = None, rel_tail: float = None) -> list:
+    """Names of the statistics of b that differ from a's by more than their
+    tolerance, relative to a's value (quantiles relative to a's median):
+    rel for the 10% and 50% quantiles, rel_mean (default rel) for the means,
+    the counts and the activations per cell, rel_tail (default rel) for the
+    90% quantiles."""
+    mean_tol = rel if rel_mean is None else rel_mean
     tail = rel if rel_tail is None else rel_tail
     bad = []
     for key in ("apd", "interval"):
@@ -79,14 +118,15 @@ def compare(a: dict, b: dict, rel: float = 0.01, rel_tail: float = None) -> list
         if sa["n"] == 0 or sb["n"] == 0:
             bad.append(key + ".n")
             continue
-        if abs(sb["n"] - sa["n"]) > rel * sa["n"]:
+        if abs(sb["n"] - sa["n"]) > mean_tol * sa["n"]:
             bad.append(key + ".n")
-        if abs(sb["mean"] - sa["mean"]) > rel * abs(sa["mean"]):
+        if abs(sb["mean"] - sa["mean"]) > mean_tol * abs(sa["mean"]):
             bad.append(key + ".mean")
         for p, r in (("p10", rel), ("p50", rel), ("p90", tail)):
             if abs(sb[p] - sa[p]) > r * abs(sa["p50"]):
                 bad.append(key + "." + p)
-    for key in ("activations_per_cell", "active_fraction"):
-        if abs(b[key] - a[key]) > rel * abs(a[key]):
-            bad.append(key)
+    if abs(b["activations_per_cell"] - a["activations_per_cell"]) > mean_tol * abs(a["activations_per_cell"]):
+        bad.append("activations_per_cell")
+    if abs(b["active_fraction"] - a["active_fraction"]) > rel * abs(a["active_fraction"]):
+        bad.append("active_fraction")
     return bad

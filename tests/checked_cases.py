@@ -75,6 +75,16 @@ def run_all() -> dict:
             for k in (1, 3):
                 run("tb_m%d_%dx%d_k%d" % (model, nx, ny, k), _problem(model, nx, ny, 1, 2, 0),
                     _state(model, nx, ny), 7, dict(schedule=2, rows=k))
+    # temporal blocking with neighbour waits between passes
+    for model in (0, 1):
+        for nx, ny in ((128, 128), (67, 45), (3, 7)):
+            run("tbn_m%d_%dx%d" % (model, nx, ny), _problem(model, nx, ny, 1, 2, 0, flags=FLAG_NEIGHBOR_SYNC),
+                _state(model, nx, ny), 7, dict(schedule=2, rows=2))
+    # four-field constants whose v^- and o switches differ (evaluated apart)
+    from paper_1309_1720_gb300 import default_params
+    prm = default_params(1)
+    prm[5] = 0.02
+    run("bocf_tho", _problem(1, 67, 45, 1, 2, 0, params=prm), _state(1, 67, 45), 6)
     # batch of uneven instances
     probs = [_problem(0, nx, ny, 0, 2, 0) for nx, ny in ((64, 64), (33, 90), (128, 20), (5, 5))]
     plan = Plan(probs)

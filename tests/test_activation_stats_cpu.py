@@ -3,7 +3,7 @@ threshold crossings are known in closed form (piecewise-linear voltage, so
 linear interpolation between samples is exact)."""
 import numpy as np
 
-from activation_stats import ActivationStats, compare
+from activation_stats import ActivationStats, compare, compare_restitution
 
 
 def _tri(t, period, phase, lo=0.0, hi=2.0):
@@ -50,5 +50,37 @@ def test_compare_flags_each_statistic():
     b["interval"]["p90"] = 112.0
     assert compare(a, b) == ["apd.mean", "interval.p90"]
     assert compare(a, b, rel_tail=0.05) == ["apd.mean"]
+    assert compare(a, b, rel_mean=0.02, rel_tail=0.05) == []
     b["activations_per_cell"] = 20.3
     assert "activations_per_cell" in compare(a, b)
+    assert "activations_per_cell" not in compare(a, b, rel_mean=0.02)
+    b["apd"]["p50"] = 47.6
+    assert "apd.p50" in compare(a, b, rel_mean=0.05, rel_tail=0.05)
+
+
+def test_restitution_bins():
+    """Beats with a known diastolic interval: each cell alternates
+    repolarisation and activation at fixed offsets, so every beat's DI and
+    APD are known; the per-bin means and counts follow."""
+    # two cells: period 40 ms with APD 30 (DI 10) and period 50 with APD 20 (DI 30)
+    periods = np.array([40.0, 50.0])
+    apds = np.array([30.0, 20.0])
+
+    def u_at(t):
+        x = np.mod(t, periods)
+        # piecewise linear: up through 1 at x = 5, down through 1 at x = 5 + apd
+        up = np.clip((x - 4.5) * 2.0, 0.0, 2.0)
+        dn = np.clip((x - (4.5 + apds)) * 2.0, 0.0, 2.0)
+        return up - dn
+    dt = 0.25
+    st = ActivationStats(u_at(0.0), 0.0, 1.0, window=(60.0, 400.0))
+    for k in range(1, 1601):
+        st.add(u_at(k * dt), k * dt)
+    r = st.restitution(width=5.0, n_bins=10)
+    assert r["n"][2] > 0 and r["n"][6] > 0 and sum(r["n"]) == r["n"][2] + r["n"][6]
+    assert abs(r["mean_apd"][2] - 30.0) <= 1e-12 and abs(r["mean_apd"][6] - 20.0) <= 1e-12
+    b = {"n": list(r["n"]), "mean_apd": list(r["mean_apd"])}
+    assert compare_restitution(r, b) == []
+    b["mean_apd"][6] = 20.3
+    assert compare_restitution(r, b) == [6]
+    assert compare_restitution(r, b, rel=0.02) == []
