@@ -264,9 +264,8 @@ __global__ void __launch_bounds__(512, 1) k_tblock(const RunArgs a, const TbArgs
             const double ca = a.cacc[s], cyv = last ? 0.0 : a.cy[s];
             // Rounds of up to blockDim cells, cell c of a round on thread c.
             // The FP64 pipe takes a warp instruction in the same time
-            // whether 1 or 32 lanes are active, so cells are packed into as
-            // few warps as possible (a warp issues on sub-partition
-            // warp mod 4: consecutive warps spread over the four).  A warp
+            // whether 1 or 32 lanes are active (measured on GB300), so
+            // cells are packed into as few warps as possible.  A warp
             // with no cell skips the round (warp-uniform); in the others
             // every lane runs, so the model's warp-uniform paths see whole
             // warps: surplus lanes repeat the round's last cell and store
