@@ -93,12 +93,13 @@ def parse():
                     help="run a short case and exit (for ncu captures): 2 steps of the 2048^2 four-field "
                          "workload in its tuned launch shape (bocf); 2 steps of the same plan on three "
                          "uniform states, one per branch of the local terms (bocf-branches); the FP64 "
-                         "DFMA, DADD and DMUL rate probes (fp64-probe); 20 steps of the 1024^2 two-field "
+                         "DFMA, DADD and DMUL rate probes and the one-lane DFMA probe (fp64-probe); 20 "
+                         "steps of the 1024^2 two-field "
                          "RK4 workload (fhn); 10 steps of the 2048^2 Karma model (karma); on the 512^2 "
                          "two-field RK4 problem 4 steps of 64 tangents (tlm) or the adjoint of 16 steps "
                          "(adj); or 200 steps of the 128^2 Euler problem with 4 steps per grid barrier (c1)")
     ap.add_argument("--experiment", default=None,
-                    choices=["all", "timing", "grid", "convergence", "orbit", "snapshots"],
+                    choices=["all", "timing", "grid", "convergence", "orbit", "snapshots", "small-grid"],
                     help="run the paper's timing / grid-size / accuracy experiments instead of the bench")
     return ap.parse_args()
 
@@ -669,6 +670,29 @@ def paper_experiments(which):
         print(json.dumps({"experiment": "time_vs_grid (Fig. 4)", "model": gname, "steps": 2000,
                           "fit": "t = a max(1, (N/N0)^2), a = median of N <= 64, b = a/N0^2 = median t/N^2 "
                                  "for N >= 2048", "results": res}), flush=True)
+    if which in ("all", "small-grid"):
+        # the 128^2 explicit-Euler workload with temporal blocking: steps per
+        # pass, block size, and grid barrier or neighbour waits between
+        # passes (best of five whole 1000-step runs; every shape must give
+        # the stage kernel's result bit for bit)
+        prob = dict(model=api.FHN, nx=128, ny=128, dx=0.04, scheme=api.EULER, dt=2e-4)
+        z = torch.from_numpy(I.fhn_broken_wave(128, 128, seed=0)).cuda()
+        ref = Plan(api.Problem(**prob)).run(z, 1000)
+        res = []
+        for flags, sync in ((0, "grid barrier"), (api.FLAG_NEIGHBOR_SYNC, "neighbour waits")):
+            for k in (2, 3, 4, 6, 8):
+                for thr in (128, 256, 512):
+                    plan = Plan(api.Problem(flags=flags, **prob), tuning=dict(schedule=2, rows=k, threads=thr))
+                    out = plan.run(z, 1000)
+                    plan.status()
+                    same = bool(torch.equal(out, ref))
+                    t = timed_step(plan, z, 1000, reps=5)
+                    plan.close()
+                    res.append({"sync": sync, "steps_per_pass": k, "threads": thr, "us_per_step": 1e6 * t,
+                                "bitwise_equal": same})
+        res.sort(key=lambda r: r["us_per_step"])
+        print(json.dumps({"experiment": "small grid: temporal blocking shapes (128^2 Euler, 1000 steps)",
+                          "results": res}), flush=True)
     if which in ("all", "snapshots"):
         # Fig. 2: voltage fields of the three models on the paper's grids
         # (FHN 384^2, Karma 256^2, BOCF 768^2), RK4, reported as the range of
@@ -809,9 +833,10 @@ def profile_case(args):
         # launches each: a warm-up half as long, then the timed one)
         L = _lib.lib()
         rate = ctypes.c_double()
-        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
-            _lib.check(L.cg_measure_fp64_rate(op, 0, ctypes.byref(rate), None))
-            print("%s %.4e per s" % (name, rate.value))
+        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul"), (6, "dfma one lane per warp")):
+            secs = ctypes.c_double()
+            _lib.check(L.cg_measure_fp64_rate(op, 0, ctypes.byref(rate), ctypes.byref(secs)))
+            print("%s %.4e per s (%.3f ms)" % (name, rate.value, 1e3 * secs.value))
         print("profile case done")
         return
     if case == "c1":

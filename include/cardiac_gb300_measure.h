@@ -25,7 +25,11 @@ enum {
     CG_MEASURE_DMUL = 2,   /* a = a * b */
     CG_MEASURE_TANH = 3,   /* a = tanh(a) * b + c (CUDA's double tanh, plus one FMA) */
     CG_MEASURE_EXP = 4,    /* a = exp(-a) * b + c (CUDA's double exp, plus one FMA) */
-    CG_MEASURE_DIV = 5     /* a = b / a + c (IEEE double division, plus one add) */
+    CG_MEASURE_DIV = 5,    /* a = b / a + c (IEEE double division, plus one add) */
+    CG_MEASURE_DFMA_ONE_LANE = 6   /* DFMA as op 0, on the first lane of each warp only (the other
+                                      31 lanes exit at once): ops_per_s counts the active lanes, so a
+                                      pipe that takes a warp instruction in the same time whatever
+                                      its active lanes reads 1/32 of op 0's rate */
 };
 
 /* Launch 4 blocks of 256 threads per SM on the current device, each thread

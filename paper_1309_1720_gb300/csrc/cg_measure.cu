@@ -12,6 +12,8 @@ namespace {
 template <int OP>
 __global__ void __launch_bounds__(256) k_fp64_rate(double *out, int64_t iters, double seed)
 {
+    // the one-lane variant: every lane but the first of each warp leaves
+    if (OP == CG_MEASURE_DFMA_ONE_LANE && (threadIdx.x & 31) != 0) return;
     double a[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) a[i] = seed + 1e-7 * threadIdx.x + 1e-3 * i;
@@ -19,7 +21,7 @@ __global__ void __launch_bounds__(256) k_fp64_rate(double *out, int64_t iters, d
     for (int64_t it = 0; it < iters; ++it) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            if (OP == CG_MEASURE_DFMA) a[i] = fma(a[i], b, c);
+            if (OP == CG_MEASURE_DFMA || OP == CG_MEASURE_DFMA_ONE_LANE) a[i] = fma(a[i], b, c);
             if (OP == CG_MEASURE_DADD) a[i] = a[i] + c;
             if (OP == CG_MEASURE_DMUL) a[i] = a[i] * b;
             if (OP == CG_MEASURE_TANH) a[i] = fma(tanh(a[i]), 1.5, c);
@@ -48,6 +50,7 @@ CG_API cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per
     case CG_MEASURE_TANH: k = (const void *)&k_fp64_rate<CG_MEASURE_TANH>; def = 2048; break;
     case CG_MEASURE_EXP: k = (const void *)&k_fp64_rate<CG_MEASURE_EXP>; def = 2048; break;
     case CG_MEASURE_DIV: k = (const void *)&k_fp64_rate<CG_MEASURE_DIV>; def = 4096; break;
+    case CG_MEASURE_DFMA_ONE_LANE: k = (const void *)&k_fp64_rate<CG_MEASURE_DFMA_ONE_LANE>; def = 40960; break;
     default: return CG_EINVAL;
     }
     if (iters <= 0) iters = def;
@@ -83,7 +86,8 @@ CG_API cg_status cg_measure_fp64_rate(int32_t op, int64_t iters, double *ops_per
         g_merr = cudaGetErrorString(e);
         return CG_ECUDA;
     }
-    const double nops = (double)grid * block * 8.0 * (double)iters;
+    const double lanes = (op == CG_MEASURE_DFMA_ONE_LANE) ? (double)block / 32.0 : (double)block;
+    const double nops = (double)grid * lanes * 8.0 * (double)iters;
     if (ops_per_s) *ops_per_s = nops / (ms * 1e-3);
     if (seconds) *seconds = ms * 1e-3;
     return CG_OK;
