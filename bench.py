@@ -305,8 +305,8 @@ def run_reference(args):
 
 def workload_config():
     return {"workload": "bocf-2048x2048-aniso9pt-rk4-5000steps",
-            "model": "Bueno-Orovio-Cherry-Fenton four-field model (Eq. bochfe), epicardial constants, H_k with "
-                     "k = 28.4",
+            "system": "Bueno-Orovio-Cherry-Fenton four-field equations (Eq. bochfe), epicardial constants, H_k "
+                      "with k = 28.4",
             "grid": [NX, NY], "dx_cm": DX, "D_cm2_per_ms": {"xx": D_XX, "yy": D_YY},
             "stencil": "9-point anisotropic diagonal tensor, alpha_d = 1/6", "bc": "no-flux mirror",
             "scheme": "RK4", "dt_ms": DT, "time_steps_per_bench_step": STEPS_PER_RUN,
