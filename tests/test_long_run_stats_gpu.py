@@ -19,12 +19,12 @@ Checks:
   90% quantiles): the same dynamical regime.
 
 Why these two levels: the whole-domain distributions of one 5 s run on a
-15 cm domain depend on where the chaotic trajectory happens to go; runs
+13 cm domain depend on where the chaotic trajectory happens to go; runs
 that differ only by rounding (GPU runs whose u differs by one ulp after S2,
 and the oracle) spread by up to 3% in the means and 8% in the 90%
 quantiles over this window.  The restitution relation is a property of the
-dynamics rather than of the trajectory: the same runs agree within 0.5% in
-its well-populated bins."""
+dynamics rather than of the trajectory: the same runs agree within 0.63%
+in its well-populated bins."""
 import json
 import os
 
