@@ -486,14 +486,15 @@ template <bool TH> struct BocfModel {
         }
     }
     // 1 / (tau1 + dtau (1 + tanh(kk (u - cc)))/2), the rates of the
-    // u-dependent time constants tau_w^- and tau_so.  In the sigmoid form
-    // s = 1/(1 + e) (a >= 0) or e/(1 + e) (a < 0), e = e^-|a|, so
-    // 1/(tau1 + dtau s) = (1 + e)/(tau1 (1 + e) + dtau sel), sel = 1 or e:
-    // one reciprocal instead of two.  With DS, ds = s (1 - s) as in
-    // half_tanh.
+    // u-dependent time constants tau_w^- and tau_so (tau2 = tau1 + dtau).
+    // In the sigmoid form s = 1/(1 + e) (a >= 0) or e/(1 + e) (a < 0),
+    // e = e^-|a|, so (tau1 + dtau s)(1 + e) is tau2 + tau1 e or
+    // tau1 + tau2 e: one FMA with its operands chosen by the sign of a (on
+    // the integer pipe), and one reciprocal, 1/(tau1 + dtau s) =
+    // (1 + e)/fma(.).  With DS, ds = s (1 - s) as in half_tanh.
     template <int IA, int IK, int IHA, int IHK, bool DS>
     __device__ __forceinline__ static double rcp_tau(const double *mp, double u, const double *tab, double tau1,
-                                                     double dtau, double &ds)
+                                                     double dtau, double tau2, double &ds)
     {
         if constexpr (TH) {
             const double t = clamp01_int(fma(mp[IHK], u, mp[IHA]));
@@ -503,12 +504,13 @@ template <bool TH> struct BocfModel {
             const double a = fma(mp[IK], u, mp[IA]);
             const double e = exp_neg(a, tab);
             const double ope = 1.0 + e;
-            const double sel = (__double_as_longlong(a) >= 0) ? dtau : dtau * e;
+            const bool pos = __double_as_longlong(a) >= 0;
+            const double ca = pos ? tau1 : tau2, cb = pos ? tau2 : tau1;
             if constexpr (DS) {
                 const double r1 = fast_rcp(ope);
                 ds = (e * r1) * r1;
             }
-            return ope * fast_rcp(fma(tau1, ope, sel));
+            return ope * fast_rcp(fma(ca, e, cb));
         }
     }
 #define CG_SW BD_AW2, BD_KW2, BD_AWH, BD_KWH
@@ -548,7 +550,7 @@ template <bool TH> struct BocfModel {
                 const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
                 const double v_inf = 1.0 - Hvm;
                 double unused;
-                const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], unused);
+                const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], mp[BP_TW2M], unused);
                 const double q = fma(-u, mp[BD_IWINF], 1.0);
                 const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
                 const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
@@ -564,7 +566,7 @@ template <bool TH> struct BocfModel {
             if (__all_sync(CG_FULL, ku >= __double_as_longlong(mp[BD_KEXC]))) {
                 // excited tissue: every switch is 1
                 double unused;
-                const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], unused);
+                const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], mp[BP_TSO2], unused);
                 const double r_s = mp[BD_RS1];
                 const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
                 const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u;
@@ -593,11 +595,11 @@ template <bool TH> struct BocfModel {
         const double r_vm = fast_rcp(tau_vm);
         const double v_inf = 1.0 - Hvm;
         double dsw = 0.0, dsso = 0.0, dss;
-        const double r_wm = rcp_tau<CG_SW, JAC>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], dsw);
+        const double r_wm = rcp_tau<CG_SW, JAC>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], mp[BP_TW2M], dsw);
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
         const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-        const double r_so = rcp_tau<CG_SSO, JAC>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], dsso);
+        const double r_so = rcp_tau<CG_SSO, JAC>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], mp[BP_TSO2], dsso);
         const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
         const double s_inf = half_tanh<CG_SS>(mp, u, c.tab, dss);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
@@ -686,11 +688,11 @@ template <bool TH> struct BocfModel {
         const double r_vm = fast_rcp(fma(Hvm, mp[BD_DTV], mp[BP_TV1M]));
         const double v_inf = 1.0 - Hvm;
         double unused;
-        const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], unused);
+        const double r_wm = rcp_tau<CG_SW, false>(mp, u, c.tab, mp[BP_TW1M], mp[BD_DTW], mp[BP_TW2M], unused);
         const double q = fma(-u, mp[BD_IWINF], 1.0);
         const double w_inf = fma(Ho, mp[BP_WINFSTAR] - q, q);
         const double r_o = fast_rcp(fma(Ho, mp[BD_DTO], mp[BP_TO1]));
-        const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], unused);
+        const double r_so = rcp_tau<CG_SSO, false>(mp, u, c.tab, mp[BP_TSO1], mp[BD_DTSO], mp[BP_TSO2], unused);
         const double r_s = fast_rcp(fma(Hw, mp[BD_DTS], mp[BP_TS1]));
         const double s_inf = half_tanh<CG_SS>(mp, u, c.tab);
         const double ua = u - mp[BP_THV], ub = mp[BP_UU] - u, uo = u - mp[BP_UO];
