@@ -344,6 +344,36 @@ cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_t check
 cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
                          int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream);
 
+/* The same gradient split at the end of the forward run, for callers that
+ * run z0 -> zT first and want the gradient later (a training step: the
+ * forward pass needs zT anyway, so it can leave the checkpoints behind and
+ * the backward pass skips cg_adjoint_run's own forward sweep: one forward
+ * run plus one adjoint run instead of two plus one).
+ *
+ * cg_adjoint_checkpoint_size: bytes of the checkpoint buffer,
+ * ceil(n_steps / c) states of round32(n_v nx ny) doubles (c as in
+ * cg_adjoint_run).
+ *
+ * cg_adjoint_forward advances z0 -> zT (device, plan layout, not
+ * overlapping each other partially nor the buffer) bit for bit as cg_run
+ * does, and keeps z0 and every c-th state in `checkpoints` (device,
+ * 256-byte aligned, caller-owned); workspace: cg_workspace_size bytes.
+ *
+ * cg_adjoint_reverse then writes lam0 and dLdD (NULL allowed) for lamT
+ * exactly as cg_adjoint_run(plan, z0, lamT, ...) would, bit for bit, from
+ * those checkpoints: same plan, n_steps and checkpoint_every, the buffer
+ * untouched in between (it is only read, so one forward serves several
+ * reverse calls); workspace: cg_adjoint_workspace_size bytes.  The plan
+ * remembers the buffers of its latest 16 cg_adjoint_forward calls with
+ * their n_steps and c: CG_EINVAL for any other buffer or count.  Other
+ * errors as cg_adjoint_run. */
+cg_status cg_adjoint_checkpoint_size(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, size_t *bytes);
+cg_status cg_adjoint_forward(cg_plan plan, const double *z0, double *zT, int64_t n_steps, int32_t checkpoint_every,
+                             double *checkpoints, void *workspace, void *stream);
+cg_status cg_adjoint_reverse(cg_plan plan, const double *checkpoints, const double *lamT, double *lam0,
+                             double *dLdD, int64_t n_steps, int32_t checkpoint_every, void *workspace,
+                             void *stream);
+
 /* ------------------------------------------------- Newton-Krylov step */
 
 /* Sect. 1 names matrix-free Newton-Krylov solvers (e.g. for periodic orbits

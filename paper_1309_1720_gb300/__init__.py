@@ -12,6 +12,6 @@ from .api import (  # noqa: F401
     ABI_VERSION, BOCF, CLAMP, DIFFUSION, EULER, FHN, HEUN, IMPLICIT_EULER, KARMA, MIRROR, PERIODIC, RK4,
     RUSH_LARSEN, STENCIL5, STENCIL9, FLAG_ALLOW_UNSTABLE, FLAG_PER_STAGE_LAUNCH, FLAG_NEIGHBOR_SYNC,
     FLAG_TANH_AS_HK, FLAG_TEST_STUCK_BARRIER,
-    DEV_NONFINITE, DEV_TIMEOUT, Linearization, Plan, Problem, default_params, n_fields, n_params,
+    Checkpoints, DEV_NONFINITE, DEV_TIMEOUT, Linearization, Plan, Problem, default_params, n_fields, n_params,
 )
 from ._lib import CGError  # noqa: F401

@@ -296,10 +296,7 @@ class Plan:
         is the same bit for bit)."""
         _state(z0, self.offsets[-1], "z0")
         _state(lamT, self.offsets[-1], "lamT")
-        sz = ctypes.c_size_t()
-        check(_lib.lib().cg_adjoint_workspace_size(self._h, int(n_steps), int(checkpoint_every), ctypes.byref(sz)))
-        if self._ws is None or self._ws.numel() < sz.value:
-            self._ws = torch.zeros(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+        self._adjoint_workspace(n_steps, checkpoint_every)
         lam0 = torch.empty_like(lamT)
         nd = 2 if self.model == FHN else 1
         dLdD = torch.empty(nd, dtype=torch.float64, device="cuda") if with_dD else None
@@ -308,6 +305,26 @@ class Plan:
                                         int(n_steps), int(checkpoint_every), self._ws.data_ptr(),
                                         _stream_handle(stream)))
         return lam0, dLdD
+
+    def forward_checkpointed(self, z0: torch.Tensor, n_steps: int, checkpoint_every: int = 0, stream=None):
+        """z0 -> zT as ``run`` (bit for bit), keeping the checkpoints a later
+        gradient needs (cg_adjoint_forward).  Returns (zT, Checkpoints);
+        ``Checkpoints.adjoint`` gives what ``adjoint`` would from z0 without
+        repeating the forward sweep."""
+        _state(z0, self.offsets[-1], "z0")
+        ck = Checkpoints(self, int(n_steps), int(checkpoint_every))
+        zT = torch.empty_like(z0)
+        check(_lib.lib().cg_adjoint_forward(self._h, z0.data_ptr(), zT.data_ptr(), ck.n_steps, ck.every,
+                                            ck.buf.data_ptr(), self.workspace().data_ptr(),
+                                            _stream_handle(stream)))
+        return zT, ck
+
+    def _adjoint_workspace(self, n_steps: int, checkpoint_every: int) -> torch.Tensor:
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_adjoint_workspace_size(self._h, int(n_steps), int(checkpoint_every), ctypes.byref(sz)))
+        if self._ws is None or self._ws.numel() < sz.value:
+            self._ws = torch.zeros(max(int(sz.value), self.workspace_bytes), dtype=torch.uint8, device="cuda")
+        return self._ws
 
     def newton_step(self, z0: torch.Tensor, period_steps: int, restart: int = 30, max_restarts: int = 1,
                     rtol: float = 1e-10, linearized: bool = False, stream=None):
@@ -343,6 +360,35 @@ class Plan:
         if raise_on_error:
             check(st)
         return int(flags.value)
+
+
+class Checkpoints:
+    """The checkpoints of one forward run z0 -> zT of a plan
+    (``Plan.forward_checkpointed``), in a device buffer of their own;
+    ``adjoint`` gives (lam0, dLdD) for a cotangent lamT = dL/dzT, bit for bit
+    those of ``Plan.adjoint(z0, lamT, ...)``, with no forward sweep
+    (cg_adjoint_reverse).  It only reads the checkpoints, so it may be called
+    several times."""
+
+    def __init__(self, plan: Plan, n_steps: int, every: int):
+        self.plan = plan
+        self.n_steps = n_steps
+        self.every = every
+        sz = ctypes.c_size_t()
+        check(_lib.lib().cg_adjoint_checkpoint_size(plan._h, n_steps, every, ctypes.byref(sz)))
+        self.buf = torch.empty(max(int(sz.value) // 8, 1), dtype=torch.float64, device="cuda")
+
+    def adjoint(self, lamT: torch.Tensor, stream=None, with_dD: bool = True):
+        p = self.plan
+        _state(lamT, p.offsets[-1], "lamT")
+        ws = p._adjoint_workspace(self.n_steps, self.every)
+        lam0 = torch.empty_like(lamT)
+        nd = 2 if p.model == FHN else 1
+        dLdD = torch.empty(nd, dtype=torch.float64, device="cuda") if with_dD else None
+        check(_lib.lib().cg_adjoint_reverse(p._h, self.buf.data_ptr(), lamT.data_ptr(), lam0.data_ptr(),
+                                            dLdD.data_ptr() if with_dD else None, self.n_steps, self.every,
+                                            ws.data_ptr(), _stream_handle(stream)))
+        return lam0, dLdD
 
 
 class Linearization:

@@ -3,9 +3,13 @@
 ``CGFlow.apply(z0, D, plan, n_steps, checkpoint_every)`` returns z(T) from the
 CUDA stepper for the diffusivities ``D`` (one per diffusive field: u and v
 for FitzHugh-Nagumo, u for the other models; each field keeps the plan's
-ratio Dyy/Dxx); its backward calls the discrete adjoint kernels with
-sqrt(T)-checkpointed recomputation (cg_adjoint_run), giving dL/dz0 and dL/dD
-(skipped when D does not require a gradient).  When ``D`` equals the plan's
+ratio Dyy/Dxx).  The forward keeps every c-th state of the run
+(cg_adjoint_forward, c = checkpoint_every, default ceil(sqrt(T))), and its
+backward sweeps back from those checkpoints with the discrete adjoint
+kernels (cg_adjoint_reverse: each segment recomputed with its stage inputs
+kept, then reversed), giving dL/dz0 and dL/dD (skipped when D does not
+require a gradient); the values are bit for bit those of cg_adjoint_run,
+without its forward sweep.  A pending backward holds ceil(T/c) states.  When ``D`` equals the plan's
 own diffusivities the plan itself runs; otherwise a plan with the same
 grid, model, scheme, ghosts and launch shape but these diffusivities is
 built (and kept for reuse with that D).
@@ -74,20 +78,14 @@ class CGFlow(torch.autograd.Function):
     def forward(ctx, z0, D, plan, n_steps, checkpoint_every=0):
         run_plan = plan_for_D(plan, D)
         z0c = z0.detach().contiguous()
-        zT = run_plan.run(z0c, int(n_steps))
-        ctx.save_for_backward(z0c)
-        ctx.plan = run_plan
-        ctx.n_steps = int(n_steps)
-        ctx.every = int(checkpoint_every)
+        zT, ctx.ckpt = run_plan.forward_checkpointed(z0c, int(n_steps), int(checkpoint_every))
         ctx.d_shape = D.shape
         return zT
 
     @staticmethod
     def backward(ctx, grad_zT):
-        (z0,) = ctx.saved_tensors
         want_dD = ctx.needs_input_grad[1]
-        lam0, dLdD = ctx.plan.adjoint(z0, grad_zT.detach().contiguous(), ctx.n_steps, ctx.every,
-                                      with_dD=want_dD)
+        lam0, dLdD = ctx.ckpt.adjoint(grad_zT.detach().contiguous(), with_dD=want_dD)
         return lam0, dLdD.reshape(ctx.d_shape) if want_dD else None, None, None, None
 
 

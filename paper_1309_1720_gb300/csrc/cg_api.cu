@@ -177,6 +177,14 @@ struct cg_plan_s {
     // workspaces linearized with this plan and their step counts (the latest
     // 16), so that cg_tlm_apply can reject a workspace it never filled
     std::vector<std::pair<const void *, int64_t>> linearized;
+    // checkpoint buffers filled by cg_adjoint_forward with this plan, with
+    // their step counts and checkpoint intervals (the latest 16), so that
+    // cg_adjoint_reverse can reject a buffer it never filled
+    struct Ckpt {
+        const void *buf;
+        int64_t n_steps, c;
+    };
+    std::vector<Ckpt> checkpointed;
 };
 
 namespace cgk {
@@ -1740,66 +1748,71 @@ CG_API cg_status cg_adjoint_workspace_size(cg_plan plan, int64_t n_steps, int32_
     return CG_OK;
 }
 
-CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
-                                int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream)
+namespace {
+
+// Common argument checks of the adjoint calls; fills L.
+cg_status adjoint_checks(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, const void *workspace,
+                         AdjLayout &L)
 {
-    cgk::NvtxRange nvtx_range("cg_adjoint_run");
     if (!plan) return fail(CG_EINVAL, "plan is NULL");
     if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
     if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
-    if (!z0 || !lamT || !lam0 || !workspace || n_steps < 0 || n_steps > MAX_STEPS || checkpoint_every < 0)
+    if (!workspace || n_steps < 0 || n_steps > MAX_STEPS || checkpoint_every < 0)
         return fail(CG_EINVAL, "bad argument");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(CG_EINVAL, "workspace must be 256-byte aligned");
-    cg_status st = check_plan_device(plan);
-    if (st != CG_OK) return st;
-    const AdjLayout L = adj_layout(plan, n_steps, checkpoint_every);
+    L = adj_layout(plan, n_steps, checkpoint_every);
     if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
+    return CG_OK;
+}
+
+// Forward segments j = 1 .. j_end - 1 of the checkpoint sweep: cp[j] is
+// c steps after cp[j-1] (cp[0] already holds z0).
+cg_status checkpoint_sweep(cg_plan plan, const AdjLayout &L, double *cp, int64_t j_end, char *ws, cudaStream_t s)
+{
+    RunArgs a;
+    for (int64_t j = 1; j < j_end; ++j) {
+        base_args(plan, a, cp + (j - 1) * L.S, cp + j * L.S, ws);
+        a.parity = (int32_t)((L.c - 1) & 1);
+        void *args[] = {&a};
+        const cg_status st = launch_stages(plan, plan->kernel, args, a, 0, L.c * plan->ns, plan->nblocks, s);
+        if (st != CG_OK) return st;
+    }
+    return CG_OK;
+}
+
+// The adjoint stage kernel of the plan, checked to fit the persistent grid.
+cg_status adjoint_kernel(cg_plan plan, const void *&ka)
+{
+    ka = lookup_adj_kernel(plan->kmodel, plan->stencil, plan->scheme, plan->cx);
+    if (!ka) return fail(CG_EUNSUPPORTED, "no adjoint kernel for this problem");
+    return check_coresident(plan, ka);
+}
+
+// The reverse part of the adjoint: given the checkpoints cp[0 .. nseg-1] of
+// z0's trajectory (c steps apart), every segment in reverse is recomputed
+// with its stage inputs kept and swept back.  The workspace's header has
+// been cleared and dLdD / the partial sums zeroed by the caller.
+cg_status adjoint_sweep_back(cg_plan plan, const AdjLayout &L, const double *cp, const double *lamT, double *lam0,
+                             double *dLdD, int64_t n_steps, char *ws, cudaStream_t s)
+{
     const Inst &I = plan->inst[0];
-    const int64_t nstate = (int64_t)plan->nv * I.nx * I.ny;
-    const size_t sbytes = (size_t)nstate * sizeof(double);
-    if (overlaps(lamT, lam0, sbytes)) return fail(CG_EINVAL, "lamT and lam0 partially overlap");
+    const size_t sbytes = (size_t)plan->nv * I.nx * I.ny * sizeof(double);
     const int nd = plan->model == CG_FHN ? 2 : 1;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    char *ws = reinterpret_cast<char *>(workspace);
-    double *cp = reinterpret_cast<double *>(ws + L.cp_off);
     double *store = reinterpret_cast<double *>(ws + L.store_off);
     double *kb = reinterpret_cast<double *>(ws + L.kb_off);
     double *part = reinterpret_cast<double *>(ws + L.part_off);
     const int nwarps = plan->nblocks * (plan->threads / 32);
-    note_run(plan, ws, s);
-    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
-    if (dLdD) {
-        if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nwarps * nd, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if (n_steps == 0) {
-        if (lam0 != lamT) e = cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
-        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
-    }
-    const void *ka = lookup_adj_kernel(plan->kmodel, plan->stencil, plan->scheme, plan->cx);
-    if (!ka) return fail(CG_EUNSUPPORTED, "no adjoint kernel for this problem");
-    st = check_coresident(plan, ka);
+    const void *ka = nullptr;
+    cg_status st = adjoint_kernel(plan, ka);
     if (st != CG_OK) return st;
-
-    // 1. forward sweep keeping a checkpoint every c steps
-    e = cudaMemcpyAsync(cp, z0, sbytes, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(checkpoint)");
-    RunArgs a;
-    for (int64_t j = 1; j < L.nseg; ++j) {
-        base_args(plan, a, cp + (j - 1) * L.S, cp + j * L.S, ws);
-        a.parity = (int32_t)((L.c - 1) & 1);
-        void *args[] = {&a};
-        st = launch_stages(plan, plan->kernel, args, a, 0, L.c * plan->ns, plan->nblocks, s);
-        if (st != CG_OK) return st;
-    }
-    // 2. lam = lamT, kh = kbar / (dt b_last) = lamT
+    // lam = lamT, kh = kbar / (dt b_last) = lamT
     double *lam = kb + 2 * L.S, *lacc = kb + 3 * L.S;
-    e = cudaMemcpyAsync(lam, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(lam, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(kb, lamT, sbytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam)");
-    // 3. segments in reverse: recompute with every stage kept, then sweep back
+    // segments in reverse: recompute with every stage kept, then sweep back
+    RunArgs a;
     int64_t r = 0;
     for (int64_t j = L.nseg - 1; j >= 0; --j) {
         const int64_t m = std::min<int64_t>(L.c, n_steps - j * L.c);
@@ -1833,7 +1846,7 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
         if (st != CG_OK) return st;
         r += m * plan->ns;
     }
-    // 4. outputs
+    // outputs
     e = cudaMemcpyAsync(lam0, lam, sbytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lam0)");
     if (!dLdD) return CG_OK;
@@ -1842,6 +1855,157 @@ CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *la
     cgk::k_reduce_partials<<<1, 32, 0, s>>>(part, nwarps, nd, inv, dLdD);
     e = cudaGetLastError();
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "reduce kernel");
+}
+
+// Clear the status header and, with dLdD, the partial sums and dLdD.
+cg_status adjoint_clear(cg_plan plan, const AdjLayout &L, double *dLdD, char *ws, cudaStream_t s)
+{
+    const int nd = plan->model == CG_FHN ? 2 : 1;
+    const int nwarps = plan->nblocks * (plan->threads / 32);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (dLdD) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.part_off, 0, sizeof(double) * (size_t)nwarps * nd, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dLdD, 0, sizeof(double) * nd, s);
+    }
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemsetAsync");
+}
+
+}  // namespace
+
+CG_API cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, double *lam0, double *dLdD,
+                                int64_t n_steps, int32_t checkpoint_every, void *workspace, void *stream)
+{
+    cgk::NvtxRange nvtx_range("cg_adjoint_run");
+    AdjLayout L;
+    cg_status st = adjoint_checks(plan, n_steps, checkpoint_every, workspace, L);
+    if (st != CG_OK) return st;
+    if (!z0 || !lamT || !lam0) return fail(CG_EINVAL, "bad argument");
+    st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    const Inst &I = plan->inst[0];
+    const size_t sbytes = (size_t)plan->nv * I.nx * I.ny * sizeof(double);
+    if (overlaps(lamT, lam0, sbytes)) return fail(CG_EINVAL, "lamT and lam0 partially overlap");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    double *cp = reinterpret_cast<double *>(ws + L.cp_off);
+    note_run(plan, ws, s);
+    st = adjoint_clear(plan, L, dLdD, ws, s);
+    if (st != CG_OK) return st;
+    cudaError_t e;
+    if (n_steps == 0) {
+        e = lam0 != lamT ? cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    const void *ka = nullptr;
+    st = adjoint_kernel(plan, ka);
+    if (st != CG_OK) return st;
+    // forward sweep keeping a checkpoint every c steps, then the sweep back
+    e = cudaMemcpyAsync(cp, z0, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(checkpoint)");
+    st = checkpoint_sweep(plan, L, cp, L.nseg, ws, s);
+    if (st != CG_OK) return st;
+    return adjoint_sweep_back(plan, L, cp, lamT, lam0, dLdD, n_steps, ws, s);
+}
+
+CG_API cg_status cg_adjoint_checkpoint_size(cg_plan plan, int64_t n_steps, int32_t checkpoint_every, size_t *bytes)
+{
+    if (!plan || !bytes || n_steps < 0 || n_steps > MAX_STEPS || checkpoint_every < 0)
+        return fail(CG_EINVAL, "bad argument");
+    if (plan->inst.size() != 1) return fail(CG_EUNSUPPORTED, "adjoint runs need a single-instance plan");
+    if (gate_scheme(plan->scheme)) return fail(CG_EUNSUPPORTED, "no adjoint of the gate integrators");
+    const AdjLayout L = adj_layout(plan, n_steps, checkpoint_every);
+    if (!L.ok) return fail(CG_EINVAL, "workspace size overflows");
+    *bytes = (size_t)L.nseg * L.S * sizeof(double);
+    return CG_OK;
+}
+
+CG_API cg_status cg_adjoint_forward(cg_plan plan, const double *z0, double *zT, int64_t n_steps,
+                                    int32_t checkpoint_every, double *checkpoints, void *workspace, void *stream)
+{
+    cgk::NvtxRange nvtx_range("cg_adjoint_forward");
+    AdjLayout L;
+    cg_status st = adjoint_checks(plan, n_steps, checkpoint_every, workspace, L);
+    if (st != CG_OK) return st;
+    if (!z0 || !zT || !checkpoints) return fail(CG_EINVAL, "bad argument");
+    if ((reinterpret_cast<uintptr_t>(checkpoints) & 255) != 0)
+        return fail(CG_EINVAL, "the checkpoint buffer must be 256-byte aligned");
+    const Inst &I = plan->inst[0];
+    const size_t sbytes = (size_t)plan->nv * I.nx * I.ny * sizeof(double);
+    const size_t cbytes = (size_t)L.nseg * L.S * sizeof(double);
+    auto range_overlap = [](const void *p, size_t n, const void *q, size_t m) {
+        const char *x = reinterpret_cast<const char *>(p), *y = reinterpret_cast<const char *>(q);
+        return x < y + m && y < x + n;
+    };
+    if (overlaps(z0, zT, sbytes)) return fail(CG_EINVAL, "z0 and zT partially overlap");
+    if (range_overlap(zT, sbytes, checkpoints, cbytes) || range_overlap(z0, sbytes, checkpoints, cbytes))
+        return fail(CG_EINVAL, "z0 or zT overlaps the checkpoint buffer");
+    st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    const void *ka = nullptr;
+    st = adjoint_kernel(plan, ka);       // the reverse sweep must be able to run
+    if (st != CG_OK) return st;
+    {
+        std::lock_guard<std::mutex> g(plan->last_mu);
+        auto &reg = plan->checkpointed;
+        auto it = std::find_if(reg.begin(), reg.end(), [&](const auto &r) { return r.buf == checkpoints; });
+        if (it != reg.end()) reg.erase(it);
+        if (reg.size() >= 16) reg.erase(reg.begin());
+        reg.push_back({checkpoints, n_steps, L.c});
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    note_run(plan, ws, s);
+    cudaError_t e = cudaMemsetAsync(ws, 0, cgk::WS_HEADER, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(checkpoints, z0, sbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(checkpoint)");
+    if (n_steps == 0) {
+        e = zT != z0 ? cudaMemcpyAsync(zT, z0, sbytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    st = checkpoint_sweep(plan, L, checkpoints, L.nseg, ws, s);
+    if (st != CG_OK) return st;
+    // the last segment ends at zT
+    const int64_t m = n_steps - (L.nseg - 1) * L.c;
+    RunArgs a;
+    base_args(plan, a, checkpoints + (L.nseg - 1) * L.S, zT, ws);
+    a.parity = (int32_t)((m - 1) & 1);
+    void *args[] = {&a};
+    return launch_stages(plan, plan->kernel, args, a, 0, m * plan->ns, plan->nblocks, s);
+}
+
+CG_API cg_status cg_adjoint_reverse(cg_plan plan, const double *checkpoints, const double *lamT, double *lam0,
+                                    double *dLdD, int64_t n_steps, int32_t checkpoint_every, void *workspace,
+                                    void *stream)
+{
+    cgk::NvtxRange nvtx_range("cg_adjoint_reverse");
+    AdjLayout L;
+    cg_status st = adjoint_checks(plan, n_steps, checkpoint_every, workspace, L);
+    if (st != CG_OK) return st;
+    if (!checkpoints || !lamT || !lam0) return fail(CG_EINVAL, "bad argument");
+    const Inst &I = plan->inst[0];
+    const size_t sbytes = (size_t)plan->nv * I.nx * I.ny * sizeof(double);
+    if (overlaps(lamT, lam0, sbytes)) return fail(CG_EINVAL, "lamT and lam0 partially overlap");
+    {
+        std::lock_guard<std::mutex> g(plan->last_mu);
+        const auto &reg = plan->checkpointed;
+        auto it = std::find_if(reg.begin(), reg.end(), [&](const auto &r) { return r.buf == checkpoints; });
+        if (it == reg.end() || it->n_steps != n_steps || it->c != L.c)
+            return fail(CG_EINVAL, "this buffer holds no checkpoints of this plan over %lld steps, %lld apart",
+                        (long long)n_steps, (long long)L.c);
+    }
+    st = check_plan_device(plan);
+    if (st != CG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    note_run(plan, ws, s);
+    st = adjoint_clear(plan, L, dLdD, ws, s);
+    if (st != CG_OK) return st;
+    if (n_steps == 0) {
+        const cudaError_t e =
+            lam0 != lamT ? cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+        return e == cudaSuccess ? CG_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    return adjoint_sweep_back(plan, L, checkpoints, lamT, lam0, dLdD, n_steps, ws, s);
 }
 
 cg_status cgk::set_last_error(cg_status st, const char *msg)

@@ -123,6 +123,15 @@ def test_linearized_tangent_entry_points_reject_null_plan(L):
                                              None, None) == 1
 
 
+def test_checkpointed_adjoint_entry_points_reject_null_plan(L):
+    """The split adjoint (forward keeping checkpoints, reverse from them)
+    checks its arguments before touching the device."""
+    sz = ctypes.c_size_t()
+    assert L.cg_adjoint_checkpoint_size(None, 10, 0, ctypes.byref(sz)) == 1
+    assert L.cg_adjoint_forward(None, None, None, 10, 0, None, None, None) == 1
+    assert L.cg_adjoint_reverse(None, None, None, None, None, 10, 0, None, None) == 1
+
+
 def test_checked_build_loads_and_exports(L):
     """The checked build (index checks in every stage worker) is a drop-in
     replacement: same exported symbols, selected by CG_BOUNDS_CHECK=1."""
