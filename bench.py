@@ -493,6 +493,21 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops, head_tuning):
     torch.cuda.synchronize()
     t_adj = e0.elapsed_time(e1) / 1e3
     plan.status()
+    # the same gradient split at the end of the forward run: the forward
+    # keeps its checkpoints (cg_adjoint_forward), the backward sweeps back
+    # from them (cg_adjoint_reverse) with no forward sweep of its own
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    zT_ck, ck = plan.forward_checkpointed(z, T)
+    e1.record()
+    lam_ck, dd_ck = ck.adjoint(lamT)
+    e2.record()
+    torch.cuda.synchronize()
+    t_fwd_ck, t_rev_ck = e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3
+    lam_ref, dd_ref = plan.adjoint(z, lamT, T)
+    split_same = bool(torch.equal(zT_ck, zT) and torch.equal(lam_ck, lam_ref) and torch.equal(dd_ck, dd_ref))
+    plan.status()
+    del ck, zT_ck, lam_ck, dd_ck, lam_ref, dd_ref
     # dL/dz0 alone (no dL/dD accumulation)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -543,6 +558,10 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops, head_tuning):
         "adjoint_seconds_T2000": t_adj,
         "adjoint_vs_plain": (n * n * T / t_adj / 1e9) / g_plain,
         "adjoint_state_only_seconds_T2000": t_adj_state,
+        "forward_checkpointed_seconds_T2000": t_fwd_ck,
+        "adjoint_reverse_from_checkpoints_seconds_T2000": t_rev_ck,
+        "forward_plus_reverse_seconds_T2000": t_fwd_ck + t_rev_ck,
+        "split_bitwise_equal_to_adjoint_run": split_same,
         "adjoint_seconds_T2000_all_stages_stored": t_adj_all,
         "adjoint_all_stages_workspace_gb": sz.value / 1e9,
         "adjoint_all_stages_vs_plain": (n * n * T / t_adj_all / 1e9) / g_plain,
@@ -552,7 +571,9 @@ def secondary_rows(torch, plan_cls, I, api, peak_tflops, head_tuning):
         "newton_gmres30_linearized_seconds": t_newton_lin,
         "newton_gmres30_linearized_bitwise_equal": newton_same,
         "note": "tlm: 64 tangents x 200 steps (rate); adjoint: full T = 2000 with ceil(sqrt(T)) checkpoints "
-                "(forward + segment recompute + reverse sweep; state_only: dL/dz0 without dL/dD), and with every stage input of the horizon "
+                "(forward + segment recompute + reverse sweep; state_only: dL/dz0 without dL/dD); split: a "
+                "forward run keeping the checkpoints, then the segment recompute + reverse sweep from them "
+                "(what an autograd backward costs), and with every stage input of the horizon "
                 "kept in HBM (forward with stores + reverse sweep); newton: one GMRES(30) cycle on the "
                 "T = 2000 flow map (wall time, 30 exact JVPs of 2000 steps each; linearized: stage "
                 "Jacobians stored by one primal run, JVPs advance the tangent alone)"}
