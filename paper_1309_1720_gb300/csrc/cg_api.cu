@@ -461,59 +461,74 @@ bool same_config(const cg_problem &a, const cg_problem &b)
     return true;
 }
 
-// Cell ranges of the G blocks of a single nx x ny instance with equal COST
-// instead of equal cell counts: every cell the adjoint's scaled (mirror
-// boundary) path handles counts 1 + beta.  Those are the cells of rows 0, 1,
-// ny-2, ny-1 and of the column strips (32*cx wide) that start at column <= 1
-// or reach column nx-2, the same test as the adjoint kernel's per-segment
-// choice.  Returns G + 1 monotone boundaries from 0 to nx*ny.
-std::vector<int64_t> cost_balanced_ranges(int nx, int ny, int tw, int G, double beta)
+// Block ranges of the static schedule: G + 1 monotone cell offsets from 0 to
+// the total cell count of the instances (in plan order, row-major inside an
+// instance).  Every offset is the start of a strip-row (the 32*cx cells of a
+// row's column strip, which one warp runs in one pass of its row loop) or
+// the end, chosen so that the blocks' summed strip-row costs are equal to
+// within one strip-row: each boundary is the strip-row start whose
+// cumulative cost is nearest to b/G of the total.  A warp takes a strip-row
+// in the same time however many of its cells it holds (the FP64 pipe is
+// warp-granular), so a cut inside a strip would charge both blocks a whole
+// strip-row.  cost(k, y, x0): the cost of strip-row (y, x0) of instance k.
+template <class Cost>
+std::vector<int64_t> strip_ranges(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int tw, int G,
+                                  Cost cost)
 {
-    std::vector<std::pair<int, int>> bstrips;           // scaled column intervals [x0, x1)
-    int64_t E = 0;                                       // scaled cells of an interior row
-    for (int x0 = 0; x0 < nx; x0 += tw)
-        if (x0 <= 1 || x0 + tw >= nx - 1) {
-            bstrips.emplace_back(x0, std::min(nx, x0 + tw));
-            E += std::min(nx, x0 + tw) - x0;
-        }
-    auto scaled_cols = [&](int64_t r) {                  // scaled cells among columns [0, r)
-        int64_t t = 0;
-        for (const auto &iv : bstrips) t += std::max<int64_t>(0, std::min<int64_t>(r, iv.second) - iv.first);
-        return t;
-    };
-    auto in_rows = [&](int64_t y) { return y <= 1 || y >= ny - 2; };
-    auto cost = [&](int64_t c) {                         // cost of cells [0, c)
-        const int64_t y = c / nx, r = c % nx;
-        const int64_t nr = std::min<int64_t>(y, 2) + std::max<int64_t>(0, y - std::max(2, ny - 2));
-        const int64_t B = nr * nx + (y - nr) * E + (r == 0 ? 0 : (in_rows(y) ? r : scaled_cols(r)));
-        return (double)c + beta * (double)B;
-    };
-    const int64_t N = (int64_t)nx * ny;
-    const double total = cost(N);
-    std::vector<int64_t> cb(G + 1, 0);
-    cb[G] = N;
-    for (int b = 1; b < G; ++b) {
-        const double target = total * b / G;
-        int64_t lo = cb[b - 1], hi = N;                  // smallest c with cost(c) >= target
-        while (lo < hi) {
-            const int64_t mid = lo + (hi - lo) / 2;
-            if (cost(mid) >= target) hi = mid; else lo = mid + 1;
-        }
-        cb[b] = lo;
+    const int n = (int)nxs.size();
+    double total = 0.0;
+    int64_t N = 0;
+    for (int k = 0; k < n; ++k) {
+        N += (int64_t)nxs[k] * nys[k];
+        for (int y = 0; y < nys[k]; ++y)
+            for (int x0 = 0; x0 < nxs[k]; x0 += tw) total += cost(k, y, x0);
+    }
+    std::vector<int64_t> cb(G + 1, N);
+    cb[0] = 0;
+    int b = 1;
+    double acc = 0.0;
+    int64_t base = 0;
+    for (int k = 0; k < n && b < G; ++k) {
+        for (int y = 0; y < nys[k] && b < G; ++y)
+            for (int x0 = 0; x0 < nxs[k]; x0 += tw) {
+                const double w = cost(k, y, x0);
+                while (b < G && total * b / G <= acc + 0.5 * w) cb[b++] = base + (int64_t)y * nxs[k] + x0;
+                acc += w;
+            }
+        base += (int64_t)nxs[k] * nys[k];
     }
     return cb;
 }
 
+// Equal strip-row counts (the forward and tangent stage kernels).
+std::vector<int64_t> static_ranges(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int tw, int G)
+{
+    return strip_ranges(nxs, nys, tw, G, [](int, int, int) { return 1.0; });
+}
+
+// The adjoint's ranges for a single nx x ny instance: a strip-row that its
+// scaled (mirror boundary) path handles costs 1 + beta.  Those are the
+// strip-rows of rows 0, 1, ny-2, ny-1 and of the column strips that start
+// at column <= 1 or reach column nx-2, the adjoint kernel's per-segment
+// test applied row by row.
+std::vector<int64_t> cost_balanced_ranges(int nx, int ny, int tw, int G, double beta)
+{
+    return strip_ranges(std::vector<int32_t>{nx}, std::vector<int32_t>{ny}, tw, G, [&](int, int y, int x0) {
+        const bool scaled = y <= 1 || y >= ny - 2 || x0 <= 1 || x0 + tw >= nx - 1;
+        return scaled ? 1.0 + beta : 1.0;
+    });
+}
+
 // Static schedule: the cells of all instances (in plan order, row-major
-// inside an instance) are cut into G equal ranges, one per block; a block's
-// range becomes column strips of 32*cx cells by row ranges, and those are
-// cut into NW pieces with equal numbers of strip-rows, one per warp.  Every
-// SM therefore gets the same FP64 work per stage, and so does each of its
-// warps (to within one row).  With ranges given (cost_balanced_ranges), the
-// blocks take those instead of equal cell counts.
+// inside an instance) are cut into G ranges at strip-row starts, one per
+// block (static_ranges: equal strip-row counts; cost_balanced_ranges for
+// the adjoint); a block's range becomes column strips of 32*cx cells by row
+// ranges, and those are cut into NW pieces with equal numbers of
+// strip-rows, one per warp.  Every SM therefore gets the same FP64 work per
+// stage, and so does each of its warps (to within one row).
 void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int cx, int G, int NW,
                      std::vector<cgk::Seg> &segs, std::vector<int32_t> &warp_seg,
-                     const std::vector<int64_t> *ranges = nullptr)
+                     const std::vector<int64_t> &ranges)
 {
     const int n = (int)nxs.size();
     std::vector<int64_t> cstart(n + 1, 0);
@@ -524,7 +539,7 @@ void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t>
     warp_seg.assign((size_t)G * NW + 1, 0);
     int k0 = 0;
     for (int b = 0; b < G; ++b) {
-        const int64_t c0 = ranges ? (*ranges)[b] : N * b / G, c1 = ranges ? (*ranges)[b + 1] : N * (b + 1) / G;
+        const int64_t c0 = ranges[b], c1 = ranges[b + 1];
         std::vector<cgk::Seg> bs;
         while (k0 < n && cstart[k0 + 1] <= c0) ++k0;
         for (int k = k0; k < n && cstart[k] < c1; ++k) {
@@ -583,19 +598,21 @@ void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t>
 // For each block of the static schedule, the range of blocks that own its
 // one-cell halo: every cell within one row and one column of the block's
 // cells, inside the same instance.  Block b owns global cells
-// [N b / G, N (b+1) / G); the owner of cell c is ceil((c+1) G / N) - 1.
+// [ranges[b], ranges[b+1]); the owner of cell c is the last block whose
+// range starts at or before c.
 void halo_dependencies(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int G,
-                       std::vector<int2> &deps)
+                       const std::vector<int64_t> &ranges, std::vector<int2> &deps)
 {
     const int n = (int)nxs.size();
     std::vector<int64_t> cstart(n + 1, 0);
     for (int k = 0; k < n; ++k) cstart[k + 1] = cstart[k] + (int64_t)nxs[k] * nys[k];
-    const int64_t N = cstart[n];
-    auto owner = [&](int64_t c) { return (int)(((c + 1) * (int64_t)G - 1) / N); };
+    auto owner = [&](int64_t c) {
+        return (int)(std::upper_bound(ranges.begin(), ranges.begin() + G, c) - ranges.begin()) - 1;
+    };
     deps.assign(G, make_int2(0, -1));
     int k0 = 0;
     for (int b = 0; b < G; ++b) {
-        const int64_t c0 = N * b / G, c1 = N * (b + 1) / G;
+        const int64_t c0 = ranges[b], c1 = ranges[b + 1];
         int lo = b, hi = b;
         while (k0 < n && cstart[k0 + 1] <= c0) ++k0;
         for (int k = k0; k < n && cstart[k] < c1; ++k) {
@@ -885,8 +902,9 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
         P->nblocks = P->num_sms * std::min(P->bpsm, occ);
         std::vector<int32_t> nxs, nys;
         for (const Inst &I : P->inst) { nxs.push_back(I.nx); nys.push_back(I.ny); }
-        static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg);
-        halo_dependencies(nxs, nys, P->nblocks, P->deps);
+        const std::vector<int64_t> rg = static_ranges(nxs, nys, 32 * P->cx, P->nblocks);
+        static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs, P->warp_seg, rg);
+        halo_dependencies(nxs, nys, P->nblocks, rg, P->deps);
         P->sync_mode = (P->sched == cgk::SCHED_STATIC && P->nblocks <= cgk::MAX_FLAG_BLOCKS &&
                         P->bc != CG_BC_PERIODIC &&
                         (P->flags & CG_FLAG_NEIGHBOR_SYNC)) ? cgk::SYNC_NEIGHBOR : cgk::SYNC_GRID;
@@ -894,7 +912,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
             P->sync_mode == cgk::SYNC_GRID) {
             const std::vector<int64_t> cb =
                 cost_balanced_ranges(nxs[0], nys[0], 32 * P->cx, P->nblocks, ADJ_BOUNDARY_COST);
-            static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs_adj, P->warp_seg_adj, &cb);
+            static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs_adj, P->warp_seg_adj, cb);
         }
     }
     if (e == cudaSuccess && P->tb_k > 0) {
@@ -2055,13 +2073,15 @@ cg_status schedule_preview(const int32_t *nx, const int32_t *ny, int32_t n_inst,
     if (adjoint) {
         if (n_inst != 1) return fail(CG_EINVAL, "the adjoint schedule is for one instance");
         cb = cost_balanced_ranges(nxs[0], nys[0], 32 * cells_x, n_blocks, ADJ_BOUNDARY_COST);
+    } else {
+        cb = static_ranges(nxs, nys, 32 * cells_x, n_blocks);
     }
-    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws, adjoint ? &cb : nullptr);
+    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws, cb);
     *n_segs = (int64_t)segs.size();
     std::copy(ws.begin(), ws.end(), warp_seg_out);
     if (deps_out) {
         std::vector<int2> deps;
-        halo_dependencies(nxs, nys, n_blocks, deps);
+        halo_dependencies(nxs, nys, n_blocks, cb, deps);
         for (int b = 0; b < n_blocks; ++b) {
             deps_out[2 * b] = deps[b].x;
             deps_out[2 * b + 1] = deps[b].y;

@@ -1,7 +1,8 @@
 """Host logic of the static schedule (no GPU): every cell of every instance is
-owned by exactly one warp segment, blocks get equal cell counts, warps inside
-a block get equal strip-rows to within one row, and each block's dependency
-range covers the owners of its whole one-cell halo."""
+owned by exactly one warp segment, blocks own consecutive ranges that start
+at strip-row starts and hold equal numbers of strip-rows (to within one),
+warps inside a block get equal strip-rows to within one row, and each
+block's dependency range covers the owners of its whole one-cell halo."""
 import ctypes
 
 import numpy as np
@@ -66,8 +67,19 @@ def test_exact_cover_and_balance(L, nxs, nys, cx, G, NW):
             per_block[w // NW] += int(blk.sum())
     for o in own:
         assert np.all(o >= 0)
-    total = sum(nx * ny for nx, ny in zip(nxs, nys))
-    assert per_block.max() - per_block.min() <= 1 + (0 if total >= G else 1)
+    # blocks own whole strip-rows, consecutive in plan order, equal in
+    # number to within one
+    flat = np.concatenate([o.reshape(-1) for o in own])
+    assert np.all(np.diff(flat) >= 0)
+    strips = np.zeros(G, dtype=np.int64)
+    for o in own:
+        ny, nx = o.shape
+        for x0 in range(0, nx, tw):
+            blk = o[:, x0:x0 + tw]
+            assert np.all(blk == blk[:, :1])
+            np.add.at(strips, blk[:, 0], 1)
+    assert strips.max() - strips.min() <= 1
+    assert per_block.sum() == flat.size
     for b in range(G):
         pw = per_warp[b * NW:(b + 1) * NW]
         assert pw.max() - pw.min() <= 1
@@ -113,8 +125,9 @@ def _scaled(nx, ny, tw):
 ])
 def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
     """Exact cover by warp segments, warps inside a block within one
-    strip-row of each other, and block costs (1.4 per scaled cell, 1
-    otherwise) equal to within one cell at each end of a block (2 x 1.4)."""
+    strip-row of each other, blocks owning whole strip-rows, and block costs
+    (1.4 per strip-row on the scaled boundary path, 1 otherwise) equal to
+    within one strip-row at each end of a block (2 x 1.4)."""
     segs, ws = adjoint_schedule(L, nx, ny, cx, G, NW)
     tw = 32 * cx
     own = np.full((ny, nx), -1, dtype=np.int64)
@@ -141,9 +154,13 @@ def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
     # blocks own consecutive row-major ranges, in block order
     flat = own.reshape(-1)
     assert np.all(np.diff(flat) >= 0)
-    cost = np.where(_scaled(nx, ny, tw), 1.4, 1.0).reshape(-1)
-    per_block = np.array([cost[flat == b].sum() for b in range(G)])
-    if nx * ny >= 4 * G:
+    scaled = _scaled(nx, ny, tw)
+    per_block = np.zeros(G)
+    for x0 in range(0, nx, tw):
+        blk = own[:, x0:x0 + tw]
+        assert np.all(blk == blk[:, :1])
+        np.add.at(per_block, blk[:, 0], np.where(scaled[:, x0], 1.4, 1.0))
+    if ny * ((nx + tw - 1) // tw) >= 4 * G:
         assert per_block.max() - per_block.min() <= 2.8 + 1e-9
 
 
