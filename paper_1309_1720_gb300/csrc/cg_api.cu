@@ -701,7 +701,76 @@ cg_status tb_setup(cg_plan_s *P)
     const int64_t per = (cells + P->num_sms - 1) / P->num_sms;
     if (single) {
         const int nx = P->inst[0].nx, ny = P->inst[0].ny;
-        int ty = (int)std::ceil(std::sqrt((double)per)), tx = ty;
+        // Tile shape with the least FP64 time on the busiest SM.  Stage g of
+        // a pass (H stages) evaluates the tile grown by H - g cells on each
+        // side, clipped to the domain and, where it reaches an edge, with
+        // its ghost ring (not at the last stage), packed into whole warps;
+        // the FP64 pipe takes a warp instruction in the same time whatever
+        // its active lanes, so a pass costs the busiest tile's sum over the
+        // stages of ceil(cells / 32) warp-evaluations.  Among the shapes from
+        // 3/4 to 3/2 of the square side that give at most one tile per SM,
+        // the cheapest wins (then the fewer tiles, then the squarer); small
+        // grids only (side <= 48), else the search below.
+        const int s0 = (int)std::ceil(std::sqrt((double)per));
+        if (s0 <= 48) {
+            auto widths = [&](int n, int t, std::vector<int> &w) {        // [tile][g - 1]
+                const int nt = (n + t - 1) / t;
+                w.assign((size_t)nt * H, 0);
+                for (int b = 0; b < nt; ++b)
+                    for (int g = 1; g <= H; ++g) {
+                        const int rad = H - g, t0 = b * t, t1 = std::min(n, t0 + t);
+                        const bool gr = g < H;
+                        const int lo = std::max(t0 - rad, 0), hi = std::min(t1 + rad, n);
+                        w[(size_t)b * H + g - 1] = (hi + (gr && hi == n)) - (lo - (gr && lo == 0));
+                    }
+                return nt;
+            };
+            int64_t best = -1;
+            int btx = 0, bty = 0, bn = 0;
+            std::vector<int> wx, wy;
+            for (int tx = std::max(1, s0 * 3 / 4); tx <= std::min(nx, s0 * 3 / 2); ++tx) {
+                const int ntx = widths(nx, tx, wx);
+                for (int ty = std::max(1, s0 * 3 / 4); ty <= std::min(ny, s0 * 3 / 2); ++ty) {
+                    const int nty = (ny + ty - 1) / ty;
+                    if ((int64_t)ntx * nty > P->num_sms) continue;
+                    widths(ny, ty, wy);
+                    int64_t worst = 0;
+                    for (int bx = 0; bx < ntx; ++bx)
+                        for (int by = 0; by < nty; ++by) {
+                            int64_t c = 0;
+                            for (int g = 0; g < H; ++g)
+                                c += ((int64_t)wx[(size_t)bx * H + g] * wy[(size_t)by * H + g] + 31) / 32;
+                            worst = std::max(worst, c);
+                        }
+                    const int n = ntx * nty;
+                    if (best < 0 || worst < best || (worst == best && n < bn) ||
+                        (worst == best && n == bn && std::abs(tx - ty) < std::abs(btx - bty))) {
+                        best = worst;
+                        btx = tx;
+                        bty = ty;
+                        bn = n;
+                    }
+                }
+            }
+            if (best >= 0) {
+                int wmax = 0;
+                int64_t ntiles = 0;
+                windows(btx, bty, wmax, ntiles);
+                const size_t smem = cgk::tb_smem_bytes(P->nv, P->ns, wmax);
+                int occ = 0;
+                if (smem + inst_smem <= (size_t)dev_smem) {
+                    const cg_status st = occupancy(smem, occ);
+                    if (st != CG_OK) return st;
+                }
+                if (occ >= 1 && ntiles <= (int64_t)occ * P->num_sms) {
+                    P->tb_tiles_x = (nx + btx - 1) / btx;
+                    P->tb_tiles_y = (ny + bty - 1) / bty;
+                    P->tb_nbr = ((P->flags & CG_FLAG_NEIGHBOR_SYNC) && ntiles <= cgk::MAX_FLAG_BLOCKS) ? 1 : 0;
+                    return finish(btx, bty, wmax, ntiles, (int)ntiles, smem);
+                }
+            }
+        }
+        int ty = s0, tx = ty;
         if (ty > ny) {
             ty = ny;
             tx = (int)((per + ny - 1) / ny);
