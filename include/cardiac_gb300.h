@@ -359,9 +359,9 @@ cg_status cg_adjoint_run(cg_plan plan, const double *z0, const double *lamT, dou
  * does, and keeps z0 and every c-th state in `checkpoints` (device,
  * 256-byte aligned, caller-owned); workspace: cg_workspace_size bytes.
  *
- * cg_adjoint_reverse then writes lam0 and dLdD (NULL allowed) for lamT
- * exactly as cg_adjoint_run(plan, z0, lamT, ...) would, bit for bit, from
- * those checkpoints: same plan, n_steps and checkpoint_every, the buffer
+ * cg_adjoint_reverse then writes lam0 (not overlapping the buffer) and
+ * dLdD (NULL allowed) for lamT exactly as cg_adjoint_run(plan, z0, lamT,
+ * ...) would, bit for bit, from those checkpoints: same plan, n_steps and checkpoint_every, the buffer
  * untouched in between (it is only read, so one forward serves several
  * reverse calls); workspace: cg_adjoint_workspace_size bytes.  The plan
  * remembers the buffers of its latest 16 cg_adjoint_forward calls with

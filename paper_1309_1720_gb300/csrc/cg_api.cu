@@ -2071,7 +2071,12 @@ CG_API cg_status cg_adjoint_reverse(cg_plan plan, const double *checkpoints, con
     if (!checkpoints || !lamT || !lam0) return fail(CG_EINVAL, "bad argument");
     const Inst &I = plan->inst[0];
     const size_t sbytes = (size_t)plan->nv * I.nx * I.ny * sizeof(double);
+    const size_t cbytes = (size_t)L.nseg * L.S * sizeof(double);
     if (overlaps(lamT, lam0, sbytes)) return fail(CG_EINVAL, "lamT and lam0 partially overlap");
+    {
+        const char *x = reinterpret_cast<const char *>(lam0), *y = reinterpret_cast<const char *>(checkpoints);
+        if (x < y + cbytes && y < x + sbytes) return fail(CG_EINVAL, "lam0 overlaps the checkpoint buffer");
+    }
     {
         std::lock_guard<std::mutex> g(plan->last_mu);
         const auto &reg = plan->checkpointed;

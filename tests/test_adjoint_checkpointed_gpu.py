@@ -100,6 +100,9 @@ def test_reverse_rejects_what_was_not_checkpointed(cuda_ok):
                                 ws.data_ptr(), None) == 1  # another plan
     # every = 0 resolves to ceil(sqrt(n)): the same checkpoints as every = 4 for n = 12
     assert rev(ck.buf, 12, 0) == 0
+    # lam0 inside the checkpoint buffer is rejected before any work
+    assert L.cg_adjoint_reverse(plan._h, ck.buf.data_ptr(), lamT.data_ptr(), ck.buf.data_ptr(), None, 12, 4,
+                                ws.data_ptr(), None) == 1
     # z0 / zT inside the checkpoint buffer are rejected before any work
     with pytest.raises(CGError):
         L2 = ck.buf.view(torch.uint8)
