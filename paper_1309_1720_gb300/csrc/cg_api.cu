@@ -525,10 +525,14 @@ std::vector<int64_t> cost_balanced_ranges(int nx, int ny, int tw, int G, double 
 // the adjoint); a block's range becomes column strips of 32*cx cells by row
 // ranges, and those are cut into NW pieces with equal numbers of
 // strip-rows, one per warp.  Every SM therefore gets the same FP64 work per
-// stage, and so does each of its warps (to within one row).
+// stage, and so does each of its warps (to within one row).  With
+// split_boundary_rows (the adjoint's schedule) no segment mixes the two
+// first or last rows of an instance with its interior rows, so that the
+// adjoint kernel's per-segment choice of its scaled boundary path matches
+// the per-row cost of cost_balanced_ranges.
 void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t> &nys, int cx, int G, int NW,
                      std::vector<cgk::Seg> &segs, std::vector<int32_t> &warp_seg,
-                     const std::vector<int64_t> &ranges)
+                     const std::vector<int64_t> &ranges, bool split_boundary_rows = false)
 {
     const int n = (int)nxs.size();
     std::vector<int64_t> cstart(n + 1, 0);
@@ -564,6 +568,19 @@ void static_schedule(const std::vector<int32_t> &nxs, const std::vector<int32_t>
                 sg.inst = k; sg.x0 = x0; sg.y0 = r0; sg.y1 = r1;
                 sg.mrow_a = ya; sg.ma0 = fa0; sg.ma1 = fa1;
                 sg.mrow_b = (yb > ya) ? yb : -1; sg.mb0 = fb0; sg.mb1 = fb1;
+                if (split_boundary_rows) {
+                    // pieces that never mix rows 0, 1 or ny-2, ny-1 with
+                    // interior rows (same rows, same order)
+                    const int ny = nys[k];
+                    for (int p : {2, ny - 2}) {
+                        if (p > sg.y0 && p <= sg.y1) {
+                            cgk::Seg head = sg;
+                            head.y1 = p - 1;
+                            bs.push_back(head);
+                            sg.y0 = p;
+                        }
+                    }
+                }
                 bs.push_back(sg);
             }
         }
@@ -981,7 +998,7 @@ cg_status make_plan(const cg_problem *probs, int32_t n_inst, const cg_tuning *tu
             P->sync_mode == cgk::SYNC_GRID) {
             const std::vector<int64_t> cb =
                 cost_balanced_ranges(nxs[0], nys[0], 32 * P->cx, P->nblocks, ADJ_BOUNDARY_COST);
-            static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs_adj, P->warp_seg_adj, cb);
+            static_schedule(nxs, nys, P->cx, P->nblocks, P->threads / 32, P->segs_adj, P->warp_seg_adj, cb, true);
         }
     }
     if (e == cudaSuccess && P->tb_k > 0) {
@@ -2150,7 +2167,7 @@ cg_status schedule_preview(const int32_t *nx, const int32_t *ny, int32_t n_inst,
     } else {
         cb = static_ranges(nxs, nys, 32 * cells_x, n_blocks);
     }
-    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws, cb);
+    static_schedule(nxs, nys, cells_x, n_blocks, warps_per_block, segs, ws, cb, adjoint);
     *n_segs = (int64_t)segs.size();
     std::copy(ws.begin(), ws.end(), warp_seg_out);
     if (deps_out) {

@@ -124,7 +124,8 @@ def _scaled(nx, ny, tw):
     (2, 2, 1, 152, 16), (3, 7, 2, 5, 4), (4096, 3, 2, 152, 16), (65, 300, 1, 13, 8),
 ])
 def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
-    """Exact cover by warp segments, warps inside a block within one
+    """Exact cover by warp segments, no segment mixing the first or last two
+    rows with interior rows, warps inside a block within one
     strip-row of each other, blocks owning whole strip-rows, and block costs
     (1.4 per strip-row on the scaled boundary path, 1 otherwise) equal to
     within one strip-row at each end of a block (2 x 1.4)."""
@@ -136,6 +137,9 @@ def test_adjoint_schedule_cover_and_cost_balance(L, nx, ny, cx, G, NW):
         for k in range(ws[w], ws[w + 1]):
             inst, x0, y0, y1, ra, a0, a1, rb, b0, b1 = segs[k]
             assert inst == 0 and x0 % tw == 0 and 0 <= y0 <= y1 < ny
+            # rows 0, 1, ny-2, ny-1 never share a segment with interior rows
+            edge = [y <= 1 or y >= ny - 2 for y in range(y0, y1 + 1)]
+            assert all(edge) or not any(edge), (y0, y1, ny)
             per_warp[w] += y1 - y0 + 1
             x1 = min(x0 + tw, nx)
             blk = np.ones((y1 - y0 + 1, x1 - x0), dtype=bool)
